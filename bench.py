@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark: triangles/s from a device-resident half-edge triangulation to
+the Polylla polygon mesh, on one or more GPUs (independent replicas).
+
+One step = polylla_generate (all five stages) + the device part of
+polylla_get_polygons on the whole mesh, inputs already in HBM.  The default
+workload is the largest single mesh: the 4096 x 4096 perturbed grid
+(33,538,050 triangles).  Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle, timed on the host
+
+Under torchrun (N > 1) every rank runs its own replica of the mesh on its own
+GPU (a single mesh does not shard); value = triangles of all ranks / max
+time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "triangles/sec to polygon mesh (device-resident), % HBM roofline; served p50/p99"
+UNIT = "triangles/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="pgrid_4096")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: the one collective is the timing max)
+# ---------------------------------------------------------------------------
+
+def dist_setup(n_gpus: int):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, ws, local
+
+
+def dist_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# measurement helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.lines:
+            return None
+        sm, mx, reasons, load_sm = [], [], set(), []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                s, m_ = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            sm.append(s)
+            mx.append(m_)
+            pw = parts[3]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+            try:
+                if float(pw) > 250.0:
+                    load_sm.append(s)
+            except ValueError:
+                pass
+        if not sm:
+            return None
+        use = load_sm if load_sm else sm
+        return {"sm_mhz": statistics.median(use), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "samples_under_load": len(load_sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_digest() -> str:
+    from paper_2403_14723_gb300 import build
+
+    return build._digest()
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary,
+    if it was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_digest") != kernel_digest():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return k.get("dram_bytes_per_launch_full_workload")
+
+
+def algorithmic_bytes(T, V, NF, P):
+    """Bytes the method must move once (next/prev of interior half-edges are
+    implicit in the layout; label bytes are L2-resident and not counted):
+    origin 12T + twin 12T + coords 16V + next/prev of frontier half-edges
+    8 N_F + CSR he_list/v_list 8 N_F + seeds/offsets 8P."""
+    per_stage = {
+        "longest_edge": 12 * T + 16 * V,          # origin + coords
+        "label_relink": 12 * T + 8 * NF,          # twin + next/prev writes
+        "chords": 0,
+        "chord_links": 0,
+        "polygons": 8 * NF + 8 * P + 4,           # he_list, v_list, seeds, offsets
+    }
+    return sum(per_stage.values()), per_stage
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def ref_sample_mesh(workload: str):
+    from paper_2403_14723_gb300 import meshgen
+
+    if workload.startswith("pgrid_"):
+        return meshgen.perturbed_grid(2048, 0.3, seed=3), "perturbed grid 2048x2048 (8,380,418 triangles), same recipe"
+    if workload == "delaunay_1m":
+        return meshgen.random_delaunay(1_000_000, seed=2), "the full 1M-point Delaunay mesh"
+    return meshgen.workload(workload), f"the full {workload} mesh"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    mesh, sample = ref_sample_mesh(args.workload)
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.run_mesh(mesh)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = mesh.n_triangles * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample, "triangles": mesh.n_triangles,
+                   "polygons": r.n_polygons},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample}; single-threaded sequential oracle, {len(times)} timed runs"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    from paper_2403_14723_gb300 import build, meshgen, polylla
+
+    rank, ws, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build_library()
+    mesh = meshgen.workload(args.workload)
+    T, V, H = mesh.n_triangles, mesh.n_vertices, mesh.n_halfedges
+    dm = polylla.DeviceMesh.from_host(mesh, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = polylla.polylla_create(dm, stream=stream)
+    lib = polylla.load_library()
+
+    def step():
+        polylla.polylla_generate(ctx, stream)
+        return polylla.polylla_get_polygons(ctx, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        out = step()
+    P, NF = out["n_polygons"], out["n_frontier"]
+
+    # ---- timed region: K steps, each bracketed by events, L2 flushed between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    torch.cuda.synchronize()
+    dist_barrier(ws)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(i)
+            starts[i].record(stream)
+            polylla.polylla_generate(ctx, stream)
+            ends[i].record(stream)
+            launches += polylla.polylla_launch_count(ctx)
+        torch.cuda.synchronize()
+    dist_barrier(ws)
+    o = polylla.polylla_get_polygons(ctx, stream)
+    assert o["n_polygons"] == P and o["n_frontier"] == NF
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = dist_max(statistics.mean(step_ms), ws)
+    value = ws * T / (ms * 1e-3)
+
+    # ---- per-kernel times (CUDA events on the launching stream) ----------
+    polylla.polylla_set_timing(ctx, True)
+    stage_acc = {}
+    for i in range(min(args.steps, 50)):
+        flush.fill_(i)
+        polylla.polylla_generate(ctx, stream)
+        for k, v in polylla.polylla_get_stage_times(ctx).items():
+            stage_acc.setdefault(k, []).append(v)
+    polylla.polylla_set_timing(ctx, False)
+    stage_ms = {k: statistics.mean(v) for k, v in stage_acc.items()}
+    total_alg, per_stage = algorithmic_bytes(T, V, NF, P)
+    dominant = max(stage_ms, key=stage_ms.get)
+    peak, peak_kind = measured_peaks()
+    ach = per_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "unit": "GB/s",
+        "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs",
+        "traffic": ncu_traffic(dominant),
+        "algorithmic_bytes": per_stage[dominant],
+        "stage_ms": stage_ms,
+        "whole_step": {"algorithmic_bytes": total_alg, "achieved": total_alg / (ms * 1e-3) / 1e9,
+                       "frac": total_alg / (ms * 1e-3) / 1e9 / peak},
+    }
+
+    # ---- end to end through the host-buffer entry point ------------------
+    e2e = None
+    if not args.no_e2e:
+        hctx = polylla.polylla_create_host(V, T, H)
+        hin = {k: torch.from_numpy(getattr(mesh, k)).pin_memory() for k in ("coords", "origin", "twin", "next", "prev")}
+        hout = {"seeds": torch.empty(T, dtype=torch.int32).pin_memory(),
+                "offsets": torch.empty(T + 1, dtype=torch.int32).pin_memory(),
+                "he_list": torch.empty(3 * T, dtype=torch.int32).pin_memory(),
+                "v_list": torch.empty(3 * T, dtype=torch.int32).pin_memory(),
+                "next": torch.empty(H, dtype=torch.int32).pin_memory(),
+                "prev": torch.empty(H, dtype=torch.int32).pin_memory()}
+        for _ in range(2):
+            polylla.polylla_generate_host(hctx, hin, hout, stream=stream)
+        e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        dist_barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            p2, nf2 = polylla.polylla_generate_host(hctx, hin, hout, stream=stream)
+        torch.cuda.synchronize()
+        dist_barrier(ws)
+        e_ms = dist_max(1e3 * (time.perf_counter() - t0) / e_steps, ws)
+        assert p2 == P and nf2 == NF
+        polylla.polylla_destroy(hctx)
+        h2d = 16 * V + 4 * 4 * H
+        d2h = 4 * (P + (P + 1) + 2 * NF + 2 * H) + 32
+        e2e = {"value": ws * T / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "polylla_generate_host (pinned host buffers, copies inside the timed region)"}
+
+    # ---- CPU baseline: the oracle, bounded sample, rank 0, N = 1 only -----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        smesh, sample = ref_sample_mesh(args.workload)
+        oracle.build()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.run_mesh(smesh)
+            ts.append(time.perf_counter() - t0)
+        cpu = {"value": smesh.n_triangles / statistics.median(ts), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sample}; median of 3 single-threaded runs on {os.cpu_count()} host cores"}
+
+    polylla.polylla_destroy(ctx)
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/int32", "data": "synthetic",
+            "config": {"workload": args.workload, "triangles": T, "vertices": V, "halfedges": H,
+                       "polygons": P, "frontier_halfedges": NF, "parallelism": f"replicas x{ws}",
+                       "l2": "256 MiB buffer written between timed steps; inputs (1.07 GB) exceed L2"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+            "kernel_digest": kernel_digest(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

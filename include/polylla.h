@@ -1,0 +1,215 @@
+/*
+ * polylla.h -- C ABI of the GB300 Polylla library (libpolylla).
+ *
+ * Turns a triangulation stored as device-resident half-edge arrays into the
+ * Polylla polygonal mesh of "GPolylla: Fully GPU-accelerated polygonal mesh
+ * generator" (arXiv 2403.14723): terminal-edge regions (Definitions 1-3,
+ * Section 3.1), joined by relinking next/prev of the frontier half-edges
+ * (Section 4.2, Fig. 3), with non-simple regions split at barrier tips
+ * (Section 5.3, Algorithm 6; Section 6.4, Algorithm 11).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - All array pointers in polylla_mesh and polylla_polygons are DEVICE
+ *   pointers of the current CUDA device; coords are float64, topology int32.
+ * - Mesh layout (the paper's implicit face indexing, Section 4.2): interior
+ *   half-edges are [0, 3T); triangle t owns 3t, 3t+1, 3t+2, counter-
+ *   clockwise, so next(e) = 3*(e/3) + (e+1)%3 and prev(e) = 3*(e/3) + (e+2)%3
+ *   for e < 3T.  Border half-edges are [3T, H): each is the twin of an
+ *   interior half-edge on the domain boundary and their next/prev walk the
+ *   exterior face.  coords is [V][2] interleaved (x, y), 16-byte aligned.
+ * - A "stream" is a cudaStream_t (NULL = the legacy default stream).  Unless
+ *   stated otherwise a call only enqueues work on that stream and returns.
+ * - Every int-returning call returns POLYLLA_OK (0) or a negative status.
+ *   Status strings come from polylla_status_string().  A context is not
+ *   thread-safe; distinct contexts are independent.
+ * - The library never falls back to the CPU: without a usable CUDA device
+ *   polylla_create fails with POLYLLA_ERR_CUDA.
+ */
+#ifndef POLYLLA_H
+#define POLYLLA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct polylla_ctx polylla_ctx;
+typedef struct CUstream_st *polylla_stream; /* same type as cudaStream_t */
+
+enum polylla_status {
+    POLYLLA_OK = 0,
+    POLYLLA_ERR_INVALID_ARGUMENT = -1, /* NULL pointer, bad size, misaligned coords  */
+    POLYLLA_ERR_INVALID_MESH = -2,     /* layout check failed at create             */
+    POLYLLA_ERR_OUT_OF_MEMORY = -3,    /* cudaMalloc failed                          */
+    POLYLLA_ERR_CUDA = -4,             /* any other CUDA error (see polylla_cuda_error) */
+    POLYLLA_ERR_NONTERMINATING = -5,   /* a rotation or cycle walk hit its cap       */
+    POLYLLA_ERR_CAPACITY = -6,         /* an internal list overflowed its capacity   */
+    POLYLLA_ERR_TIMEOUT = -7,          /* a device wait gave up (scan look-back)     */
+};
+
+/* Input mesh (device arrays owned by the caller). */
+typedef struct {
+    int32_t n_vertices;   /* V >= 3                                     */
+    int32_t n_triangles;  /* T >= 1, 3T < 2^31                          */
+    int32_t n_halfedges;  /* H = 3T + number of border half-edges (>= 3) */
+    const double *coords; /* [V][2] float64, 16-byte aligned            */
+    const int32_t *origin; /* [H] vertex each half-edge leaves           */
+    const int32_t *twin;   /* [H] opposite half-edge                      */
+    int32_t *next;         /* [H] read by create's layout check; generate  */
+    int32_t *prev;         /* [H] rewrites entries [0, 3T) (see below)     */
+} polylla_mesh;
+
+typedef struct {
+    int32_t validate;      /* nonzero: check the mesh layout at create (default on) */
+    int32_t max_rotation;  /* cap on one vertex rotation (0: 4096)               */
+} polylla_options;
+
+/* Output polygons (device arrays owned by the context). */
+typedef struct {
+    int32_t n_polygons;       /* P                                           */
+    int32_t n_frontier;       /* N_F = total polygon length                  */
+    const int32_t *seeds;     /* [P]   smallest half-edge of each polygon, ascending */
+    const int32_t *offsets;   /* [P+1] polygon p is he_list[offsets[p] .. offsets[p+1]) */
+    const int32_t *he_list;   /* [N_F] half-edges of each polygon from its seed along next */
+    const int32_t *v_list;    /* [N_F] origin of each listed half-edge        */
+} polylla_polygons;
+
+/*
+ * polylla_create -- validate a mesh and allocate every buffer generate needs.
+ *   out    receives the new context (NULL on failure).
+ *   mesh   device arrays, not copied: they must stay valid and keep their
+ *          layout until polylla_destroy.  coords/origin/twin are only read.
+ *   opt    NULL for defaults.
+ *   stream used for the layout check; create synchronizes this stream.
+ * Allocates scratch and output buffers sized from V, T and H (about
+ * 8 bytes per triangle of scratch plus 4*(T + T+1 + 3T + 3T) bytes of
+ * output); polylla_generate then allocates and frees nothing (the paper's
+ * point in Section 4.2: the method runs in the input's own memory).
+ * Errors: INVALID_ARGUMENT, INVALID_MESH (twin not an involution without
+ * fixed points, interior next/prev not the implicit triangle layout,
+ * origin(next e) != origin(twin e), border links inconsistent, an index
+ * out of range, a non-finite coordinate), OUT_OF_MEMORY, CUDA.
+ */
+int polylla_create(polylla_ctx **out, const polylla_mesh *mesh,
+                   const polylla_options *opt, polylla_stream stream);
+
+/*
+ * polylla_generate -- run the whole method on the context's mesh.
+ * Enqueues, on stream, the five stages of the hot path:
+ *   (1) longest edge of each triangle (Algorithm 2 / 8): squared float64
+ *       lengths dx*dx + dy*dy, each operation rounded to nearest, no FMA;
+ *       equal lengths go to the smaller edge id min(e, twin e);
+ *   (2) frontier labels (Algorithm 3 / 9): e is frontier iff e or twin(e)
+ *       is a border half-edge, or neither is a longest edge;
+ *   (3) terminal and border-terminal seeds (Algorithm 4 / 10);
+ *   (4) relinking (Section 4.2, Algorithm 5 / 12): for every frontier
+ *       interior half-edge e, next(e) = the first frontier half-edge met
+ *       rotating clockwise about target(e) from the triangle's next, and
+ *       prev of that half-edge = e;
+ *   (5) repair (Algorithm 6 / 11): a vertex with one frontier edge f is a
+ *       barrier tip of degree d; its chord is CW^r(f), r = floor((d-1)/2)+1,
+ *       found with the stage-2 labels; chords join the frontier and the
+ *       links around their endpoints are redone; then every polygon (each
+ *       cycle of next) is found, keyed by its smallest half-edge and written
+ *       as a scan-compacted CSR list (Section 6.8).
+ * On completion next/prev of every interior half-edge [0, 3T) hold the
+ * polygon mesh: polygon links for frontier half-edges, the triangle links
+ * for the rest (the values create validated).  Border half-edges are not
+ * written.  The input next/prev of interior half-edges are never read, so
+ * generate may be called again on the same mesh and gives the same result.
+ * Asynchronous; no allocation, no host synchronization.  Device-side
+ * failures (NONTERMINATING, CAPACITY, TIMEOUT) are recorded in the context
+ * and reported by polylla_get_polygons / polylla_last_error.
+ */
+int polylla_generate(polylla_ctx *ctx, polylla_stream stream);
+
+/*
+ * polylla_get_polygons -- read the polygon count and hand out the CSR.
+ * Copies 16 bytes device->host on stream and synchronizes it.  The device
+ * arrays stay owned by the context and valid until the next generate or
+ * destroy.  Returns the recorded device status if the last generate failed.
+ */
+int polylla_get_polygons(polylla_ctx *ctx, polylla_polygons *out, polylla_stream stream);
+
+/* Status of the last generate (synchronizes the context's last stream). */
+int polylla_last_error(polylla_ctx *ctx);
+
+/* CUDA error code behind the last POLYLLA_ERR_CUDA (cudaError_t as int). */
+int polylla_cuda_error(polylla_ctx *ctx);
+
+/* Free every buffer of the context (synchronizes the device first). */
+void polylla_destroy(polylla_ctx *ctx);
+
+/* Static string for a status code. */
+const char *polylla_status_string(int status);
+
+/*
+ * Intermediate labels, for stage-by-stage checks (not needed to use the
+ * output).  Device arrays owned by the context, valid after a generate
+ * completes and until the next generate or destroy:
+ *   longest_local [T] uint8: local index k (0..2) of triangle t's longest
+ *                 half-edge 3t+k (stage 1);
+ *   flags [T] uint8: bits 0-2 frontier after repair (F1) of 3t+k, bits 3-5
+ *                 frontier of stage 2 (F0), bit 6 set when the triangle's
+ *                 longest half-edge is the seed of its terminal-edge region
+ *                 (stage 3);
+ *   tips [n_tips] int32: for each barrier tip, the stage-2 frontier
+ *                 half-edge leaving it (order unspecified);
+ *   chords [n_tips] int32: the chord half-edge leaving the same tip.
+ * n_tips is copied to the host (synchronizes stream).
+ */
+typedef struct {
+    const uint8_t *longest_local;
+    const uint8_t *flags;
+    const int32_t *tips;
+    const int32_t *chords;
+    int32_t n_tips;
+} polylla_labels;
+int polylla_get_labels(polylla_ctx *ctx, polylla_labels *out, polylla_stream stream);
+
+/*
+ * Host-buffer path (end-to-end use): a context that owns device copies of
+ * the mesh.  polylla_create_host allocates device arrays for a mesh of the
+ * given sizes (no data yet); polylla_generate_host copies the host mesh in,
+ * generates, and copies the polygons and the rewritten next/prev back.
+ * Host buffers should be pinned (cudaHostAlloc) for full copy speed; any
+ * host memory works.  Capacities of the outputs: seeds T, offsets T+1,
+ * he_list and v_list 3T, next and prev H.  *n_polygons and *n_frontier
+ * receive P and N_F.  Synchronizes stream before returning.
+ */
+typedef struct {
+    const double *coords;
+    const int32_t *origin, *twin, *next, *prev;
+} polylla_host_mesh;
+typedef struct {
+    int32_t *seeds, *offsets, *he_list, *v_list;
+    int32_t *next, *prev;
+    int32_t n_polygons, n_frontier;
+} polylla_host_result;
+int polylla_create_host(polylla_ctx **out, int32_t n_vertices, int32_t n_triangles,
+                        int32_t n_halfedges, const polylla_options *opt);
+int polylla_generate_host(polylla_ctx *ctx, const polylla_host_mesh *in,
+                          polylla_host_result *out, int32_t validate, polylla_stream stream);
+
+/*
+ * Per-stage timing.  With timing enabled, generate records a CUDA event
+ * around each kernel it launches (on the generate stream);
+ * polylla_get_stage_times synchronizes and writes the milliseconds of up to
+ * n stages of the last generate, returning how many it wrote.
+ * polylla_stage_name gives the kernel name of stage i.
+ * polylla_launch_count gives the number of kernels the last generate
+ * launched.
+ */
+int polylla_set_timing(polylla_ctx *ctx, int32_t enable);
+int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
+int polylla_stage_count(void);
+const char *polylla_stage_name(int32_t i);
+int polylla_launch_count(polylla_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYLLA_H */

@@ -1,0 +1,267 @@
+// Label-phase kernels: mesh layout check, longest edge per triangle
+// (stage 1), and the fused frontier / seed / relink pass (stages 2-4).
+#include "polylla_internal.cuh"
+
+namespace polylla {
+
+// ===========================================================================
+// Layout check (create only).  One thread per half-edge; any violation sets
+// *bad.  Checks the contract the hot path relies on instead of re-reading
+// next/prev: the implicit triangle layout of interior half-edges, a twin
+// involution without fixed points, consistent border links, indices in
+// range, target consistency and finite coordinates.
+// ===========================================================================
+__global__ void k_validate(MeshView m, int32_t *bad) {
+    const int32_t HI = 3 * m.T;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t fail = 0;
+    if (i < m.V) {
+        double2 p = m.xy[i];
+        fail |= !isfinite(p.x) || !isfinite(p.y);
+    }
+    if (i < m.H) {
+        int32_t e = (int32_t)i;
+        int32_t t = m.twin[e];
+        int32_t o = m.origin[e];
+        int32_t n = m.next[e];
+        int32_t p = m.prev[e];
+        fail |= t < 0 || t >= m.H || t == e;
+        fail |= o < 0 || o >= m.V;
+        fail |= n < 0 || n >= m.H || p < 0 || p >= m.H;
+        if (!fail) {
+            fail |= m.twin[t] != e;
+            fail |= m.prev[n] != e;
+            // target(e) = origin(twin e) = origin(next e)
+            fail |= m.origin[n] != m.origin[t];
+            if (e < HI) {
+                fail |= n != nx_of(e) || p != pv_of(e);
+            } else {
+                fail |= t >= HI || n < HI || p < HI;
+            }
+        }
+    }
+    if (fail) atomicOr(bad, 1);
+}
+
+void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s) {
+    int64_t n = m.H > m.V ? m.H : m.V;
+    int blocks = (int)((n + 255) / 256);
+    k_validate<<<blocks, 256, 0, s>>>(m, bad);
+}
+
+// ===========================================================================
+// Stage 1: longest edge of each triangle (Algorithm 2 / Algorithm 8).
+//
+// The reference value is the float64 squared length
+//     d = fl(fl(dx*dx) + fl(dy*dy)),  dx = fl(xb - xa),  dy = fl(yb - ya),
+// and the longest edge is the largest d, equal d going to the smaller edge id
+// min(e, twin e).  GB300 issues float64 at a small fraction of its float32
+// rate, so the argmax is first decided by a certified float32 filter and
+// only triangles the filter cannot decide take the float64 path.
+//
+// Filter.  Each coordinate x is truncated to float32 (x^ keeps the top 23
+// significand bits, so |x^ - x| <= 2^-23 |x| = 2u|x| with u = 2^-24, and
+// |x^| <= |x|) by bit manipulation (no float64 instruction); coordinates
+// outside [2^-126, 2^60) in magnitude (zero included) send the triangle to
+// the float64 path.  With S = |x^a| + |x^b| the float32 difference
+// dx^ = fl32(x^b - x^a) satisfies |dx^ - dx| <= 3.0001 u Sx, hence
+//   |D^ - d| <= 6.0003u (Sx|dx^| + Sy|dy^|) + 9.0007u^2 (Sx^2 + Sy^2)
+//               + 2.0002u D^ + (float64 rounding of d, < 2^-50 d)
+// where D^ = fl32(fl32(dx^ dx^) + fl32(dy^ dy^)).  The bound used,
+//   B = 6.1u m1 + 9.1u^2 m2 + 4.5u D^ + 2^-118,
+// adds 2.5u D^ for the rounding of the final comparison and an absolute
+// term for float32 underflow.  If D^max - Bmax > D^j + Bj for the other two
+// edges, the float64 argmax is the same edge and has no tie.
+// ===========================================================================
+
+__device__ __forceinline__ float trunc_to_f32(double v, uint32_t &bad) {
+    uint32_t hi = (uint32_t)__double2hiint(v);
+    uint32_t lo = (uint32_t)__double2loint(v);
+    uint32_t mag = hi & 0x7FFFFFFFu;
+    // biased float64 exponent must lie in [897, 1083]: |v| in [2^-126, 2^60)
+    bad |= (uint32_t)((mag - (897u << 20)) >= ((1084u - 897u) << 20));
+    // (hi:lo) << 3 puts the low 9 exponent bits at 31..23 and the top 23
+    // significand bits at 22..0; subtracting 384 from that 9-bit field
+    // rebiases 1023 -> 127 for exponents in range
+    uint32_t bits = __funnelshift_l(lo, hi, 3) - (384u << 23);
+    bits |= hi & 0x80000000u;
+    return __uint_as_float(bits);
+}
+
+struct EdgeF32 {
+    float d;   // D^
+    float b;   // error bound B
+};
+
+__device__ __forceinline__ EdgeF32 edge_f32(float ax, float ay, float bx, float by) {
+    const float u = 5.9604644775390625e-08f;  // 2^-24
+    float dx = __fsub_rn(bx, ax);
+    float dy = __fsub_rn(by, ay);
+    float sx = __fadd_rn(fabsf(ax), fabsf(bx));
+    float sy = __fadd_rn(fabsf(ay), fabsf(by));
+    EdgeF32 r;
+    r.d = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    float m1 = fmaf(sx, fabsf(dx), sy * fabsf(dy));
+    float m2 = fmaf(sx, sx, sy * sy);
+    r.b = fmaf(6.1f * u, m1, fmaf(9.1f * u * u, m2, fmaf(4.5f * u, r.d, 3.0e-36f)));
+    return r;
+}
+
+__device__ __forceinline__ double sq_len_f64(double2 a, double2 b) {
+    double dx = __dsub_rn(b.x, a.x);
+    double dy = __dsub_rn(b.y, a.y);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__device__ __noinline__ uint32_t longest_exact(double2 p0, double2 p1, double2 p2, int32_t e0,
+                                               const int32_t *__restrict__ twin) {
+    double d0 = sq_len_f64(p0, p1);
+    double d1 = sq_len_f64(p1, p2);
+    double d2 = sq_len_f64(p2, p0);
+    double d[3] = {d0, d1, d2};
+    uint32_t best = 0;
+#pragma unroll
+    for (uint32_t k = 1; k < 3; k++) {
+        if (d[k] > d[best]) {
+            best = k;
+        } else if (d[k] == d[best]) {
+            int32_t ek = e0 + (int32_t)k, eb = e0 + (int32_t)best;
+            int32_t tk = twin[ek], tb = twin[eb];
+            int32_t ik = ek < tk ? ek : tk;
+            int32_t ib = eb < tb ? eb : tb;
+            if (ik < ib) best = k;
+        }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(256) k_longest_edge(MeshView m, Work w) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    // reset this generate's control block and scan look-back words
+    if (t < w.n_tiles) w.tile_status[t] = 0ull;
+    if (t < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[t] = 0;
+    if (t >= m.T) return;
+    const int32_t e0 = 3 * t;
+    const int32_t a0 = __ldg(m.origin + e0);
+    const int32_t a1 = __ldg(m.origin + e0 + 1);
+    const int32_t a2 = __ldg(m.origin + e0 + 2);
+    const double2 p0 = __ldg(m.xy + a0);
+    const double2 p1 = __ldg(m.xy + a1);
+    const double2 p2 = __ldg(m.xy + a2);
+    uint32_t bad = 0;
+    float x0 = trunc_to_f32(p0.x, bad), y0 = trunc_to_f32(p0.y, bad);
+    float x1 = trunc_to_f32(p1.x, bad), y1 = trunc_to_f32(p1.y, bad);
+    float x2 = trunc_to_f32(p2.x, bad), y2 = trunc_to_f32(p2.y, bad);
+    EdgeF32 g0 = edge_f32(x0, y0, x1, y1);
+    EdgeF32 g1 = edge_f32(x1, y1, x2, y2);
+    EdgeF32 g2 = edge_f32(x2, y2, x0, y0);
+    uint32_t k;
+    float dm, bm, dA, bA, dB, bB;
+    if (g0.d >= g1.d && g0.d >= g2.d) {
+        k = 0; dm = g0.d; bm = g0.b; dA = g1.d; bA = g1.b; dB = g2.d; bB = g2.b;
+    } else if (g1.d >= g2.d) {
+        k = 1; dm = g1.d; bm = g1.b; dA = g0.d; bA = g0.b; dB = g2.d; bB = g2.b;
+    } else {
+        k = 2; dm = g2.d; bm = g2.b; dA = g0.d; bA = g0.b; dB = g1.d; bB = g1.b;
+    }
+    float lo = __fsub_rn(dm, bm);
+    bool sure = !bad && lo > __fadd_rn(dA, bA) && lo > __fadd_rn(dB, bB);
+    if (!sure) k = longest_exact(p0, p1, p2, e0, m.twin);
+    w.le[t] = (uint8_t)k;
+}
+
+void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
+    int blocks = (m.T + 255) / 256;
+    k_longest_edge<<<blocks, 256, 0, s>>>(m, w);
+}
+
+// ===========================================================================
+// Stages 2-4 fused: frontier labels (Algorithm 3 / 9), seeds (Algorithm 4 /
+// 10) and the relink of every frontier half-edge (Section 4.2; the per-half-
+// edge form of Algorithm 12), one thread per triangle.
+//
+//   F0[e] = border(e) or (not LE[e] and not LE[twin e])
+//   seed  = the triangle's longest half-edge e when it is the smaller half of
+//           a terminal edge (LE[e] and LE[twin e]) or lies on the border
+//   next[e] for frontier e: x = next(e); while not F0[x]: x = CW(x) =
+//           next(twin x); then next[e] = x, prev[x] = e.  Non-frontier e get
+//           their triangle links.  A rotation that comes back to twin(e)
+//           means target(e) has one frontier edge: a barrier tip, recorded
+//           with the frontier half-edge twin(e) leaving it.
+//
+// F0 of a half-edge in another triangle is evaluated on the fly from the
+// longest-edge bytes (L2-resident) and that half-edge's twin, which the
+// rotation needs anyway, so the twin array is read from HBM once.
+// In place is race-free: the rotation reads only twin and le; each next[e]
+// is written by e's own thread and each prev[x] by the unique e with
+// next[e] = x (or by x's own thread when x is not frontier).
+// ===========================================================================
+__global__ void __launch_bounds__(256) k_label_relink(MeshView m, Work w) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int32_t HI = 3 * m.T;
+    const int32_t e0 = 3 * t;
+    int32_t tw[3];
+    tw[0] = __ldg(m.twin + e0);
+    tw[1] = __ldg(m.twin + e0 + 1);
+    tw[2] = __ldg(m.twin + e0 + 2);
+    const uint32_t lt = w.le[t];
+    uint32_t F = 0, twle = 0, lnb[3];
+#pragma unroll
+    for (uint32_t k = 0; k < 3; k++) {
+        const bool b = tw[k] >= HI;
+        const uint32_t ln = b ? 3u : (uint32_t)w.le[tri_of(tw[k])];
+        lnb[k] = ln;
+        const bool tl = !b && ln == (uint32_t)loc_of(tw[k]);
+        const bool f = b || (lt != k && !tl);
+        F |= (uint32_t)f << k;
+        twle |= (uint32_t)tl << k;
+    }
+    const bool seed = (tw[lt] >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < tw[lt]);
+    w.flags[t] = (uint8_t)(F | (F << 3) | ((uint32_t)seed << 6));
+
+#pragma unroll
+    for (uint32_t k = 0; k < 3; k++) {
+        const int32_t e = e0 + (int32_t)k;
+        const uint32_t j = k == 2 ? 0u : k + 1;
+        if (!((F >> k) & 1u)) {
+            m.next[e] = e0 + (int32_t)j;
+            m.prev[e] = e0 + (int32_t)(k == 0 ? 2 : k - 1);
+            continue;
+        }
+        int32_t x = e0 + (int32_t)j;
+        if (!((F >> j) & 1u)) {
+            // cross the non-frontier edge x into the neighbouring triangle
+            int32_t y = tw[j];            // interior: non-frontier edges are not border
+            uint32_t lny = lnb[j];        // le of tri(y)
+            int32_t steps = 0;
+            while (true) {
+                x = nx_of(y);
+                const int32_t tx = __ldg(m.twin + x);
+                if (tx >= HI) break;      // border edge: frontier
+                const uint32_t lnt = w.le[tri_of(tx)];
+                if (lny != (uint32_t)loc_of(x) && lnt != (uint32_t)loc_of(tx)) break;  // frontier
+                y = tx;
+                lny = lnt;
+                if (++steps > w.max_rot) {
+                    atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
+                    break;
+                }
+            }
+        }
+        m.next[e] = x;
+        m.prev[x] = e;
+        if (x == tw[k]) {
+            const int32_t slot = atomicAdd(&w.ctrl->n_tips, 1);
+            if (slot < w.tip_cap) w.tips[slot] = tw[k];
+            else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+        }
+    }
+}
+
+void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
+    int blocks = (m.T + 255) / 256;
+    k_label_relink<<<blocks, 256, 0, s>>>(m, w);
+}
+
+}  // namespace polylla

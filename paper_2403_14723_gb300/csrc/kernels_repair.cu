@@ -1,0 +1,113 @@
+// Repair-phase kernels (stage 5a): chords from barrier tips and the relink
+// around their endpoints.  Both run over the (short) tip list with a
+// persistent grid-stride loop, so a mesh without tips costs two tiny
+// launches.
+#include "polylla_internal.cuh"
+
+namespace polylla {
+
+__device__ __forceinline__ bool f1_of(const uint8_t *__restrict__ flags, int32_t e, int32_t HI) {
+    if (e >= HI) return true;  // border half-edges are always frontier
+    return (flags[tri_of(e)] >> loc_of(e)) & 1u;
+}
+
+__device__ __forceinline__ void set_f1(uint8_t *flags, int32_t e) {
+    const int32_t t = tri_of(e);
+    unsigned int *word = reinterpret_cast<unsigned int *>(flags) + (t >> 2);
+    atomicOr(word, 1u << (8 * (t & 3) + loc_of(e)));
+}
+
+// ===========================================================================
+// Chords (Algorithm 6 first part / Algorithm 11).  For the tip b left by
+// the unique stage-2 frontier half-edge f: count the degree d by rotating
+// clockwise (CW(y) = next(twin y)) until f comes back, then the chord is
+// m = CW^r(f) with r = floor((d-1)/2) + 1 (the inclusive loop "for 0 to
+// (degree-1)/2").  Both halves of m join the frontier (F1).  Tips come only
+// from the stage-2 labels, so the result does not depend on the order in
+// which tips are processed.
+// ===========================================================================
+__global__ void __launch_bounds__(256) k_chords(MeshView m, Work w) {
+    const int32_t HI = 3 * m.T;
+    int32_t n = w.ctrl->n_tips;
+    if (n > w.tip_cap) n = w.tip_cap;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t f = w.tips[i];
+        int32_t y = f, d = 0;
+        bool ok = true;
+        do {
+            const int32_t ty = __ldg(m.twin + y);
+            if (ty >= HI || ++d > w.max_rot) { ok = false; break; }
+            y = nx_of(ty);
+        } while (y != f);
+        if (!ok) {
+            atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
+            w.chords[i] = -1;
+            continue;
+        }
+        const int32_t r = (d - 1) / 2 + 1;
+        y = f;
+        for (int32_t s = 0; s < r; s++) y = nx_of(__ldg(m.twin + y));
+        w.chords[i] = y;
+        set_f1(w.flags, y);
+        set_f1(w.flags, __ldg(m.twin + y));
+    }
+}
+
+void launch_chords(const MeshView &m, const Work &w, cudaStream_t s) {
+    k_chords<<<w.persistent_blocks, 256, 0, s>>>(m, w);
+}
+
+// ===========================================================================
+// Links around chord endpoints.  Around a vertex the relink pairs each
+// frontier half-edge o leaving it with the next frontier half-edge leaving
+// it in clockwise order: next[twin o] = that half-edge.  A chord half-edge c
+// inserts itself into that order, so only the two links touching c change:
+//   after c : y = first F1 half-edge clockwise from c  -> next[twin c] = y
+//   before c: z = first F1 half-edge counter-clockwise from c (CCW(z) =
+//             twin(prev z)) -> next[twin z] = c
+// Every other link keeps its stage-4 value.  Two chords at one vertex write
+// the link between them with the same value, so no ordering is needed.
+// ===========================================================================
+__device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, int32_t c, int32_t HI) {
+    // clockwise neighbour
+    int32_t tc = __ldg(m.twin + c);
+    int32_t y = nx_of(tc);
+    int32_t steps = 0;
+    while (!f1_of(w.flags, y, HI)) {
+        y = nx_of(__ldg(m.twin + y));
+        if (++steps > w.max_rot) { atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING); return; }
+    }
+    m.next[tc] = y;
+    m.prev[y] = tc;
+    // counter-clockwise neighbour; reaching a border half-edge z means the
+    // interior half-edge before it, pv, is twin(z)
+    int32_t pv = pv_of(c);
+    int32_t z = __ldg(m.twin + pv);
+    steps = 0;
+    while (!f1_of(w.flags, z, HI)) {
+        pv = pv_of(z);
+        z = __ldg(m.twin + pv);
+        if (++steps > w.max_rot) { atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING); return; }
+    }
+    // twin(z) == pv
+    m.next[pv] = c;
+    m.prev[c] = pv;
+}
+
+__global__ void __launch_bounds__(256) k_chord_links(MeshView m, Work w) {
+    const int32_t HI = 3 * m.T;
+    int32_t n = w.ctrl->n_tips;
+    if (n > w.tip_cap) n = w.tip_cap;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n; i += gridDim.x * blockDim.x) {
+        const int32_t c0 = w.chords[i >> 1];
+        if (c0 < 0) continue;
+        const int32_t c = (i & 1) ? __ldg(m.twin + c0) : c0;
+        relink_around(m, w, c, HI);
+    }
+}
+
+void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s) {
+    k_chord_links<<<w.persistent_blocks, 256, 0, s>>>(m, w);
+}
+
+}  // namespace polylla

@@ -1,0 +1,329 @@
+"""Thin Python binding of libpolylla (``include/polylla.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device arrays are torch CUDA tensors (PyTorch supplies device
+memory and streams); functions keep the C names.  If the library has not
+been built, or no CUDA device is usable, calls raise -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+POLYLLA_OK = 0
+STATUS = {
+    0: "ok", -1: "invalid argument", -2: "invalid mesh layout", -3: "out of device memory",
+    -4: "CUDA error", -5: "rotation or cycle walk did not terminate",
+    -6: "internal list capacity exceeded", -7: "device wait timed out",
+}
+
+
+class PolyllaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status})")
+
+
+class polylla_mesh(ctypes.Structure):
+    _fields_ = [
+        ("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32), ("n_halfedges", ctypes.c_int32),
+        ("coords", ctypes.c_void_p), ("origin", ctypes.c_void_p), ("twin", ctypes.c_void_p),
+        ("next", ctypes.c_void_p), ("prev", ctypes.c_void_p),
+    ]
+
+
+class polylla_options(ctypes.Structure):
+    _fields_ = [("validate", ctypes.c_int32), ("max_rotation", ctypes.c_int32)]
+
+
+class polylla_polygons(ctypes.Structure):
+    _fields_ = [
+        ("n_polygons", ctypes.c_int32), ("n_frontier", ctypes.c_int32),
+        ("seeds", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+        ("he_list", ctypes.c_void_p), ("v_list", ctypes.c_void_p),
+    ]
+
+
+class polylla_labels(ctypes.Structure):
+    _fields_ = [
+        ("longest_local", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+        ("tips", ctypes.c_void_p), ("chords", ctypes.c_void_p), ("n_tips", ctypes.c_int32),
+    ]
+
+
+class polylla_host_mesh(ctypes.Structure):
+    _fields_ = [("coords", ctypes.c_void_p), ("origin", ctypes.c_void_p), ("twin", ctypes.c_void_p),
+                ("next", ctypes.c_void_p), ("prev", ctypes.c_void_p)]
+
+
+class polylla_host_result(ctypes.Structure):
+    _fields_ = [("seeds", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("he_list", ctypes.c_void_p),
+                ("v_list", ctypes.c_void_p), ("next", ctypes.c_void_p), ("prev", ctypes.c_void_p),
+                ("n_polygons", ctypes.c_int32), ("n_frontier", ctypes.c_int32)]
+
+
+# every function the header declares, with its ctypes signature
+_SIGNATURES = {
+    "polylla_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_mesh),
+                                      ctypes.POINTER(polylla_options), ctypes.c_void_p]),
+    "polylla_generate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polylla_get_polygons": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_polygons), ctypes.c_void_p]),
+    "polylla_last_error": (ctypes.c_int, [ctypes.c_void_p]),
+    "polylla_cuda_error": (ctypes.c_int, [ctypes.c_void_p]),
+    "polylla_destroy": (None, [ctypes.c_void_p]),
+    "polylla_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "polylla_get_labels": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_labels), ctypes.c_void_p]),
+    "polylla_create_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.POINTER(polylla_options)]),
+    "polylla_generate_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_host_mesh),
+                                             ctypes.POINTER(polylla_host_result), ctypes.c_int32, ctypes.c_void_p]),
+    "polylla_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "polylla_get_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
+    "polylla_stage_count": (ctypes.c_int, []),
+    "polylla_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "polylla_launch_count": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libpolylla.so (built by ``build.build_library``); raise if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    so = path or _build.library_path()
+    if not os.path.exists(so):
+        raise RuntimeError(f"libpolylla is not built ({so} missing); run paper_2403_14723_gb300.build.build_library()")
+    lib = ctypes.CDLL(so)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != POLYLLA_OK:
+        raise PolyllaError(rc, where)
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, n):
+    import torch
+
+    if not t.is_cuda:
+        raise ValueError("device array expected (torch CUDA tensor)")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"expected contiguous {dtype} tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _CudaArray:
+    """Zero-copy view of context-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {
+            "shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3, "strides": None,
+        }
+
+
+def _view(ptr, n, typestr, dtype):
+    import torch
+
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_CudaArray(int(ptr), int(n), typestr), device="cuda")
+
+
+@dataclass
+class DeviceMesh:
+    """The five device arrays of one mesh (torch CUDA tensors)."""
+
+    coords: "object"   # [V, 2] float64
+    origin: "object"   # [H] int32
+    twin: "object"
+    next: "object"
+    prev: "object"
+    n_triangles: int
+
+    @classmethod
+    def from_host(cls, mesh, device="cuda"):
+        import torch
+
+        return cls(
+            coords=torch.from_numpy(mesh.coords).to(device).contiguous(),
+            origin=torch.from_numpy(mesh.origin).to(device),
+            twin=torch.from_numpy(mesh.twin).to(device),
+            next=torch.from_numpy(mesh.next).to(device),
+            prev=torch.from_numpy(mesh.prev).to(device),
+            n_triangles=int(mesh.n_triangles),
+        )
+
+
+def polylla_create(mesh: DeviceMesh, validate: bool = True, max_rotation: int = 0, stream=None) -> int:
+    """Create a context on a device mesh; returns the context handle."""
+    import torch
+
+    lib = load_library()
+    V = mesh.coords.shape[0]
+    H = mesh.origin.numel()
+    m = polylla_mesh(V, int(mesh.n_triangles), H,
+                     _dev_ptr(mesh.coords.view(-1), torch.float64, 2 * V),
+                     _dev_ptr(mesh.origin, torch.int32, H), _dev_ptr(mesh.twin, torch.int32, H),
+                     _dev_ptr(mesh.next, torch.int32, H), _dev_ptr(mesh.prev, torch.int32, H))
+    opt = polylla_options(1 if validate else 0, int(max_rotation))
+    ctx = ctypes.c_void_p()
+    _check(lib.polylla_create(ctypes.byref(ctx), ctypes.byref(m), ctypes.byref(opt), _stream_ptr(stream)),
+           "polylla_create")
+    return ctx.value
+
+
+def polylla_generate(ctx: int, stream=None) -> None:
+    _check(load_library().polylla_generate(ctypes.c_void_p(ctx), _stream_ptr(stream)), "polylla_generate")
+
+
+def polylla_get_polygons(ctx: int, stream=None) -> dict:
+    """Return ``{n_polygons, n_frontier, seeds, offsets, he_list, v_list}``
+    with zero-copy int32 CUDA tensors over the context's buffers."""
+    import torch
+
+    out = polylla_polygons()
+    _check(load_library().polylla_get_polygons(ctypes.c_void_p(ctx), ctypes.byref(out), _stream_ptr(stream)),
+           "polylla_get_polygons")
+    P, NF = out.n_polygons, out.n_frontier
+    return {
+        "n_polygons": P, "n_frontier": NF,
+        "seeds": _view(out.seeds, P, "<i4", torch.int32),
+        "offsets": _view(out.offsets, P + 1, "<i4", torch.int32),
+        "he_list": _view(out.he_list, NF, "<i4", torch.int32),
+        "v_list": _view(out.v_list, NF, "<i4", torch.int32),
+    }
+
+
+def polylla_get_labels(ctx: int, n_triangles: int, stream=None) -> dict:
+    import torch
+
+    out = polylla_labels()
+    _check(load_library().polylla_get_labels(ctypes.c_void_p(ctx), ctypes.byref(out), _stream_ptr(stream)),
+           "polylla_get_labels")
+    return {
+        "longest_local": _view(out.longest_local, n_triangles, "|u1", torch.uint8),
+        "flags": _view(out.flags, n_triangles, "|u1", torch.uint8),
+        "tips": _view(out.tips, out.n_tips, "<i4", torch.int32),
+        "chords": _view(out.chords, out.n_tips, "<i4", torch.int32),
+        "n_tips": out.n_tips,
+    }
+
+
+def polylla_last_error(ctx: int) -> int:
+    return load_library().polylla_last_error(ctypes.c_void_p(ctx))
+
+
+def polylla_cuda_error(ctx: int) -> int:
+    return load_library().polylla_cuda_error(ctypes.c_void_p(ctx))
+
+
+def polylla_destroy(ctx: int) -> None:
+    if ctx:
+        load_library().polylla_destroy(ctypes.c_void_p(ctx))
+
+
+def polylla_status_string(status: int) -> str:
+    return load_library().polylla_status_string(int(status)).decode()
+
+
+def polylla_set_timing(ctx: int, enable: bool) -> None:
+    _check(load_library().polylla_set_timing(ctypes.c_void_p(ctx), 1 if enable else 0), "polylla_set_timing")
+
+
+def polylla_get_stage_times(ctx: int) -> dict:
+    lib = load_library()
+    n = lib.polylla_stage_count()
+    buf = (ctypes.c_float * n)()
+    k = lib.polylla_get_stage_times(ctypes.c_void_p(ctx), buf, n)
+    if k < 0:
+        raise PolyllaError(k, "polylla_get_stage_times")
+    return {lib.polylla_stage_name(i).decode(): float(buf[i]) for i in range(k)}
+
+
+def polylla_stage_count() -> int:
+    return load_library().polylla_stage_count()
+
+
+def polylla_stage_name(i: int) -> str:
+    return load_library().polylla_stage_name(int(i)).decode()
+
+
+def polylla_launch_count(ctx: int) -> int:
+    return load_library().polylla_launch_count(ctypes.c_void_p(ctx))
+
+
+def polylla_create_host(n_vertices: int, n_triangles: int, n_halfedges: int, max_rotation: int = 0) -> int:
+    lib = load_library()
+    opt = polylla_options(0, int(max_rotation))
+    ctx = ctypes.c_void_p()
+    _check(lib.polylla_create_host(ctypes.byref(ctx), int(n_vertices), int(n_triangles), int(n_halfedges),
+                                   ctypes.byref(opt)), "polylla_create_host")
+    return ctx.value
+
+
+def polylla_generate_host(ctx: int, host_in: dict, host_out: dict, validate: bool = False, stream=None) -> tuple:
+    """Host-buffer path.  ``host_in``: coords/origin/twin/next/prev CPU
+    tensors (pinned for speed); ``host_out``: seeds/offsets/he_list/v_list/
+    next/prev CPU int32 tensors of the documented capacities.  Returns
+    ``(n_polygons, n_frontier)``."""
+    lib = load_library()
+    hm = polylla_host_mesh(*(ctypes.c_void_p(host_in[k].data_ptr()) for k in ("coords", "origin", "twin", "next", "prev")))
+    hr = polylla_host_result(*(ctypes.c_void_p(host_out[k].data_ptr())
+                               for k in ("seeds", "offsets", "he_list", "v_list", "next", "prev")), 0, 0)
+    _check(lib.polylla_generate_host(ctypes.c_void_p(ctx), ctypes.byref(hm), ctypes.byref(hr),
+                                     1 if validate else 0, _stream_ptr(stream)), "polylla_generate_host")
+    return hr.n_polygons, hr.n_frontier
+
+
+class Polylla:
+    """Owns one context on a device mesh (convenience wrapper)."""
+
+    def __init__(self, mesh: DeviceMesh, validate: bool = True, max_rotation: int = 0, stream=None):
+        self.mesh = mesh
+        self.ctx = polylla_create(mesh, validate=validate, max_rotation=max_rotation, stream=stream)
+
+    def generate(self, stream=None):
+        polylla_generate(self.ctx, stream)
+
+    def polygons(self, stream=None) -> dict:
+        return polylla_get_polygons(self.ctx, stream)
+
+    def labels(self, stream=None) -> dict:
+        return polylla_get_labels(self.ctx, self.mesh.n_triangles, stream)
+
+    def close(self):
+        polylla_destroy(self.ctx)
+        self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.ctx:
+                self.close()
+        except Exception:
+            pass

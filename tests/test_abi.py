@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+``include/polylla.h`` declares (no GPU needed: nothing here launches work)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2403_14723_gb300 import build, polylla
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "polylla.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(polylla_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return build.build_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("polylla_create", "polylla_generate", "polylla_get_polygons", "polylla_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(polylla_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_covers_every_symbol():
+    assert set(declared_functions()) == set(polylla._SIGNATURES)
+
+
+def test_status_strings_without_gpu(lib_path):
+    lib = polylla.load_library()
+    assert lib.polylla_status_string(0) == b"ok"
+    assert lib.polylla_status_string(-2) == b"invalid mesh layout"
+    assert lib.polylla_stage_count() == 5
+    names = [lib.polylla_stage_name(i).decode() for i in range(5)]
+    assert names == ["longest_edge", "label_relink", "chords", "chord_links", "polygons"]
+
+
+def test_null_arguments_rejected_without_gpu(lib_path):
+    lib = polylla.load_library()
+    ctx = ctypes.c_void_p()
+    assert lib.polylla_create(None, None, None, None) == -1
+    assert lib.polylla_create(ctypes.byref(ctx), None, None, None) == -1
+    m = polylla.polylla_mesh(3, 1, 2, None, None, None, None, None)   # H < 3T + 3
+    assert lib.polylla_create(ctypes.byref(ctx), ctypes.byref(m), None, None) == -1
+    assert lib.polylla_generate(None, None) == -1
+    assert lib.polylla_get_polygons(None, None, None) == -1
+
+
+def test_built_for_sm_103a_only():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
