@@ -127,7 +127,7 @@ int polylla_generate(polylla_ctx *ctx, polylla_stream stream);
 
 /*
  * polylla_get_polygons -- read the polygon count and hand out the CSR.
- * Copies 16 bytes device->host on stream and synchronizes it.  The device
+ * Copies 32 bytes device->host on stream and synchronizes it.  The device
  * arrays stay owned by the context and valid until the next generate or
  * destroy.  Returns the recorded device status if the last generate failed.
  */
@@ -151,10 +151,10 @@ const char *polylla_status_string(int status);
  * completes and until the next generate or destroy:
  *   longest_local [T] uint8: local index k (0..2) of triangle t's longest
  *                 half-edge 3t+k (stage 1);
- *   flags [T] uint8: bits 0-2 frontier after repair (F1) of 3t+k, bits 3-5
- *                 frontier of stage 2 (F0), bit 6 set when the triangle's
- *                 longest half-edge is the seed of its terminal-edge region
- *                 (stage 3);
+ *   flags [T] uint8: bits 0-2 frontier after repair (F1) of 3t+k (the
+ *                 stage-2 frontier F0 is F1 without the chord half-edges),
+ *                 bits 3-5 zero, bit 6 set when the triangle's longest
+ *                 half-edge is the seed of its terminal-edge region (stage 3);
  *   tips [n_tips] int32: for each barrier tip, the stage-2 frontier
  *                 half-edge leaving it (order unspecified);
  *   chords [n_tips] int32: the chord half-edge leaving the same tip.

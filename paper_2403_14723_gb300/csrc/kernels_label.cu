@@ -135,26 +135,15 @@ __device__ __noinline__ uint32_t longest_exact(double2 p0, double2 p1, double2 p
     return best;
 }
 
-__global__ void __launch_bounds__(256) k_longest_edge(MeshView m, Work w) {
-    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    // reset this generate's control block and scan look-back words
-    if (t < w.n_tiles) w.tile_status[t] = 0ull;
-    if (t < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[t] = 0;
-    if (t >= m.T) return;
-    const int32_t e0 = 3 * t;
-    const int32_t a0 = __ldg(m.origin + e0);
-    const int32_t a1 = __ldg(m.origin + e0 + 1);
-    const int32_t a2 = __ldg(m.origin + e0 + 2);
-    const double2 p0 = __ldg(m.xy + a0);
-    const double2 p1 = __ldg(m.xy + a1);
-    const double2 p2 = __ldg(m.xy + a2);
+__device__ __forceinline__ uint32_t longest_of(double2 p0, double2 p1, double2 p2, int32_t e0,
+                                               const int32_t *__restrict__ twin) {
     uint32_t bad = 0;
-    float x0 = trunc_to_f32(p0.x, bad), y0 = trunc_to_f32(p0.y, bad);
-    float x1 = trunc_to_f32(p1.x, bad), y1 = trunc_to_f32(p1.y, bad);
-    float x2 = trunc_to_f32(p2.x, bad), y2 = trunc_to_f32(p2.y, bad);
-    EdgeF32 g0 = edge_f32(x0, y0, x1, y1);
-    EdgeF32 g1 = edge_f32(x1, y1, x2, y2);
-    EdgeF32 g2 = edge_f32(x2, y2, x0, y0);
+    const float x0 = trunc_to_f32(p0.x, bad), y0 = trunc_to_f32(p0.y, bad);
+    const float x1 = trunc_to_f32(p1.x, bad), y1 = trunc_to_f32(p1.y, bad);
+    const float x2 = trunc_to_f32(p2.x, bad), y2 = trunc_to_f32(p2.y, bad);
+    const EdgeF32 g0 = edge_f32(x0, y0, x1, y1);
+    const EdgeF32 g1 = edge_f32(x1, y1, x2, y2);
+    const EdgeF32 g2 = edge_f32(x2, y2, x0, y0);
     uint32_t k;
     float dm, bm, dA, bA, dB, bB;
     if (g0.d >= g1.d && g0.d >= g2.d) {
@@ -164,15 +153,96 @@ __global__ void __launch_bounds__(256) k_longest_edge(MeshView m, Work w) {
     } else {
         k = 2; dm = g2.d; bm = g2.b; dA = g0.d; bA = g0.b; dB = g1.d; bB = g1.b;
     }
-    float lo = __fsub_rn(dm, bm);
-    bool sure = !bad && lo > __fadd_rn(dA, bA) && lo > __fadd_rn(dB, bB);
-    if (!sure) k = longest_exact(p0, p1, p2, e0, m.twin);
-    w.le[t] = (uint8_t)k;
+    const float lo = __fsub_rn(dm, bm);
+    const bool sure = !bad && lo > __fadd_rn(dA, bA) && lo > __fadd_rn(dB, bB);
+    if (!sure) k = longest_exact(p0, p1, p2, e0, twin);
+    return k;
+}
+
+// Persistent CTAs walk 1024-triangle tiles.  The origin triples of the next
+// tile are bulk-copied (TMA engine, cp.async.bulk + mbarrier) into the other
+// half of a two-stage shared-memory ring while the current tile computes, so
+// the HBM stream of origin never waits on the coordinate gathers.  Each
+// thread takes 4 triangles (strided by 256, so a warp's gathers and byte
+// stores stay contiguous) and issues their 12 coordinate loads together.
+__global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w) {
+    __shared__ __align__(128) int32_t s_org[2][3 * LE_TILE];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    // reset this generate's control block and scan look-back words
+    const int32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t gsz = gridDim.x * blockDim.x;
+    for (int32_t i = gtid; i < w.n_tiles; i += gsz) w.tile_status[i] = 0ull;
+    if (gtid < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[gtid] = 0;
+
+    const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // the copy may round the tail up to 16 bytes: at most 3 ints past 3T,
+    // inside origin because H >= 3T + 3 (checked at create)
+    auto issue = [&](int32_t tile, int st) {
+        const int32_t t0 = tile * LE_TILE;
+        const int32_t nt = min(LE_TILE, m.T - t0);
+        const uint32_t bytes = ((uint32_t)(12 * nt) + 15u) & ~15u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar[st], bytes);
+        bulk_load(s_org[st], m.origin + 3 * (int64_t)t0, bytes, &s_bar[st]);
+    };
+    int32_t tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < n_tiles) issue(tile, 0);
+    uint32_t parity = 0u;  // bit st = parity to wait for on stage st
+    constexpr int PER = LE_TILE / LE_THREADS;
+    for (int it = 0; tile < n_tiles; it++, tile += gridDim.x) {
+        const int st = it & 1;
+        const int32_t nxt = tile + gridDim.x;
+        if (threadIdx.x == 0 && nxt < n_tiles) issue(nxt, st ^ 1);
+        const bool ok = mbar_wait(&s_bar[st], (parity >> st) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // give up: record it, wait (bounded) for this block's copies in
+            // flight so no bulk copy lands after the block has left, return
+            if (threadIdx.x == 0) atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
+            mbar_wait(&s_bar[st], (parity >> st) & 1u);
+            if (nxt < n_tiles) mbar_wait(&s_bar[st ^ 1], (parity >> (st ^ 1)) & 1u);
+            return;
+        }
+        parity ^= 1u << st;
+        const int32_t t0 = tile * LE_TILE;
+        const int32_t *so = s_org[st];
+        double2 p[PER][3];
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int32_t lt = threadIdx.x + q * LE_THREADS;
+            if (t0 + lt < m.T) {
+                p[q][0] = __ldg(m.xy + so[3 * lt]);
+                p[q][1] = __ldg(m.xy + so[3 * lt + 1]);
+                p[q][2] = __ldg(m.xy + so[3 * lt + 2]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int32_t lt = threadIdx.x + q * LE_THREADS;
+            const int32_t t = t0 + lt;
+            if (t < m.T) w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t, m.twin);
+        }
+        __syncthreads();  // stage st is refilled next iteration
+    }
+}
+
+int longest_edge_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_longest_edge, LE_THREADS, 0) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
 }
 
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
-    int blocks = (m.T + 255) / 256;
-    k_longest_edge<<<blocks, 256, 0, s>>>(m, w);
+    const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;
+    int blocks = n_tiles < w.le_blocks ? n_tiles : w.le_blocks;
+    // the control-block reset needs >= 8 threads and covers the look-back
+    // words with a grid-stride loop, so any grid >= 1 works
+    k_longest_edge<<<blocks, LE_THREADS, 0, s>>>(m, w);
 }
 
 // ===========================================================================
@@ -191,58 +261,68 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 //
 // F0 of a half-edge in another triangle is evaluated on the fly from the
 // longest-edge bytes (L2-resident) and that half-edge's twin, which the
-// rotation needs anyway, so the twin array is read from HBM once.
+// rotation loads anyway, so the twin array is read from HBM once and no
+// frontier array is needed.  Twin values are split into (triangle, corner)
+// once, so a rotation step costs one twin and one byte load.
 // In place is race-free: the rotation reads only twin and le; each next[e]
 // is written by e's own thread and each prev[x] by the unique e with
 // next[e] = x (or by x's own thread when x is not frontier).
 // ===========================================================================
-__global__ void __launch_bounds__(256) k_label_relink(MeshView m, Work w) {
+__device__ __forceinline__ int32_t div3(int32_t x) { return x / 3; }
+
+__global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w) {
     const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
     const int32_t HI = 3 * m.T;
     const int32_t e0 = 3 * t;
-    int32_t tw[3];
+    int32_t tw[3], ttri[3];
+    uint32_t tloc[3], lnb[3];
     tw[0] = __ldg(m.twin + e0);
     tw[1] = __ldg(m.twin + e0 + 1);
     tw[2] = __ldg(m.twin + e0 + 2);
     const uint32_t lt = w.le[t];
-    uint32_t F = 0, twle = 0, lnb[3];
+    uint32_t F = 0, twle = 0;
 #pragma unroll
-    for (uint32_t k = 0; k < 3; k++) {
+    for (int k = 0; k < 3; k++) {
         const bool b = tw[k] >= HI;
-        const uint32_t ln = b ? 3u : (uint32_t)w.le[tri_of(tw[k])];
-        lnb[k] = ln;
-        const bool tl = !b && ln == (uint32_t)loc_of(tw[k]);
-        const bool f = b || (lt != k && !tl);
-        F |= (uint32_t)f << k;
+        ttri[k] = div3(tw[k]);
+        tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
+        lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
+        const bool tl = !b && lnb[k] == tloc[k];
+        F |= (uint32_t)(b || ((uint32_t)k != lt && !tl)) << k;
         twle |= (uint32_t)tl << k;
     }
-    const bool seed = (tw[lt] >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < tw[lt]);
-    w.flags[t] = (uint8_t)(F | (F << 3) | ((uint32_t)seed << 6));
-
+    const int32_t twl = lt == 0u ? tw[0] : (lt == 1u ? tw[1] : tw[2]);
+    const bool seed = (twl >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < twl);
+    w.flags[t] = (uint8_t)(F | ((uint32_t)seed << 6));
 #pragma unroll
-    for (uint32_t k = 0; k < 3; k++) {
-        const int32_t e = e0 + (int32_t)k;
-        const uint32_t j = k == 2 ? 0u : k + 1;
+    for (int k = 0; k < 3; k++) {
+        const int32_t e = e0 + k;
+        const int j = k == 2 ? 0 : k + 1;
         if (!((F >> k) & 1u)) {
-            m.next[e] = e0 + (int32_t)j;
-            m.prev[e] = e0 + (int32_t)(k == 0 ? 2 : k - 1);
+            m.next[e] = e0 + j;
+            m.prev[e] = e0 + (k == 0 ? 2 : k - 1);
             continue;
         }
-        int32_t x = e0 + (int32_t)j;
+        int32_t x = e0 + j;
         if (!((F >> j) & 1u)) {
             // cross the non-frontier edge x into the neighbouring triangle
-            int32_t y = tw[j];            // interior: non-frontier edges are not border
-            uint32_t lny = lnb[j];        // le of tri(y)
+            int32_t ty = ttri[j];      // twin of x, interior: non-frontier is not border
+            uint32_t ly = tloc[j];
+            uint32_t ley = lnb[j];     // le of tri(y)
             int32_t steps = 0;
             while (true) {
-                x = nx_of(y);
+                const uint32_t lx = ly == 2u ? 0u : ly + 1u;
+                x = 3 * ty + (int32_t)lx;               // next(y), in tri(y)
                 const int32_t tx = __ldg(m.twin + x);
-                if (tx >= HI) break;      // border edge: frontier
-                const uint32_t lnt = w.le[tri_of(tx)];
-                if (lny != (uint32_t)loc_of(x) && lnt != (uint32_t)loc_of(tx)) break;  // frontier
-                y = tx;
-                lny = lnt;
+                if (tx >= HI) break;                     // border edge: frontier
+                const int32_t ttx = div3(tx);
+                const uint32_t ltx = (uint32_t)(tx - 3 * ttx);
+                const uint32_t lex = w.le[ttx];
+                if (ley != lx && lex != ltx) break;      // neither half longest: frontier
+                ty = ttx;
+                ly = ltx;
+                ley = lex;
                 if (++steps > w.max_rot) {
                     atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
                     break;
@@ -260,8 +340,8 @@ __global__ void __launch_bounds__(256) k_label_relink(MeshView m, Work w) {
 }
 
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
-    int blocks = (m.T + 255) / 256;
-    k_label_relink<<<blocks, 256, 0, s>>>(m, w);
+    int blocks = (m.T + RL_THREADS - 1) / RL_THREADS;
+    k_label_relink<<<blocks, RL_THREADS, 0, s>>>(m, w);
 }
 
 }  // namespace polylla

@@ -11,11 +11,13 @@ __device__ __forceinline__ bool f1_of(const uint8_t *__restrict__ flags, int32_t
     return (flags[tri_of(e)] >> loc_of(e)) & 1u;
 }
 
-__device__ __forceinline__ void set_f1(uint8_t *flags, int32_t e) {
+__device__ __forceinline__ void set_flag_bit(uint8_t *flags, int32_t e, int shift) {
     const int32_t t = tri_of(e);
     unsigned int *word = reinterpret_cast<unsigned int *>(flags) + (t >> 2);
-    atomicOr(word, 1u << (8 * (t & 3) + loc_of(e)));
+    atomicOr(word, 1u << (8 * (t & 3) + shift + loc_of(e)));
 }
+// F1 bit (bits 0-2) of half-edge e
+__device__ __forceinline__ void set_f1(uint8_t *flags, int32_t e) { set_flag_bit(flags, e, 0); }
 
 // ===========================================================================
 // Chords (Algorithm 6 first part / Algorithm 11).  For the tip b left by

@@ -114,6 +114,8 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
+    c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
+    if (polygons_configure() != 0) return cuda_fail(c, cudaGetLastError());
     c->w.max_rot = (opt && opt->max_rotation > 0) ? opt->max_rotation : 4096;
     for (int i = 0; i <= kStages; i++) {
         e = cudaEventCreate(&c->ev[i]);

@@ -4,7 +4,6 @@
 // generate; nothing is allocated on the hot path):
 //   le      [T]   uint8  local index of each triangle's longest half-edge
 //   flags   [T]   uint8  bits 0-2 F1 (frontier after repair) of 3t+k,
-//                        bits 3-5 F0 (frontier of the label phase),
 //                        bit 6 the triangle's longest half-edge is a seed
 //   tips    [V]   int32  F0 half-edge leaving each barrier tip
 //   chords  [V]   int32  chord half-edge leaving each barrier tip
@@ -58,12 +57,69 @@ struct Work {
     DevCtrl *ctrl;
     int32_t max_rot;
     int32_t persistent_blocks;   // grid of the sparse (tip) kernels
+    int32_t le_blocks;           // grid of the persistent longest-edge kernel
 };
 
-// polygon kernel tiling: 256 threads x 8 consecutive half-edges
+// polygon kernel tiling: 2048 consecutive half-edges per 256-thread block;
+// the tile's CSR output is staged in shared memory up to POLY_BUF entries
 constexpr int POLY_THREADS = 256;
 constexpr int POLY_ITEMS = 8;
 constexpr int POLY_TILE = POLY_THREADS * POLY_ITEMS;
+constexpr int POLY_BUF = 1024;
+
+// longest-edge kernel: persistent CTAs, 512-triangle tiles of origin
+// bulk-copied (TMA) into a two-stage shared-memory ring
+constexpr int LE_THREADS = 256;
+constexpr int LE_TILE = 512;
+
+// relink kernel: one thread per triangle
+constexpr int RL_THREADS = 256;
+
+// bounded waits: iterations of an mbarrier try_wait loop before giving up
+constexpr int MBAR_WAIT_LIMIT = 1 << 22;
+
+// ---- bulk copies (TMA engine) and mbarriers, inline PTX --------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase of the given parity; false after MBAR_WAIT_LIMIT tries
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < MBAR_WAIT_LIMIT; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 
 // ---- implicit triangle layout (paper Section 4.2) -------------------------
 __device__ __forceinline__ int32_t tri_of(int32_t e) { return e / 3; }
@@ -82,9 +138,11 @@ __device__ __forceinline__ int32_t pv_of(int32_t e) {
 // launchers (each enqueues one kernel on stream)
 void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s);
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s);
+int longest_edge_blocks_per_sm();
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chords(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_polygons(const MeshView &m, const Work &w, cudaStream_t s);
+int polygons_configure();  // opt in to the polygon kernel's dynamic shared memory
 
 }  // namespace polylla

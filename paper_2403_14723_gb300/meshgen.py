@@ -347,6 +347,23 @@ def lattice_delaunay(n_points: int, side: int, seed: int) -> HalfEdgeMesh:
     return build_halfedges(tris, pts, name=f"lattice_delaunay_{n_points}_{side}_s{seed}")
 
 
+def near_tie_delaunay(n_points: int, side: int, seed: int, ulps: int = 4) -> HalfEdgeMesh:
+    """Lattice Delaunay mesh (see :func:`lattice_delaunay`) whose coordinates
+    are then moved by a few units in the last place and scaled into
+    ``[0, 1)``: squared edge lengths that were equal now differ only in
+    their last bits, so a float32 screen of the longest edge cannot decide
+    them and the exact float64 comparison must."""
+    m = lattice_delaunay(n_points, side, seed)
+    rng = np.random.default_rng(seed + 7)
+    xy = m.coords / float(side) + 0.25
+    bits = xy.view(np.int64) + rng.integers(-ulps, ulps + 1, size=xy.shape)
+    xy = bits.view(np.float64)
+    tri = m.triangles()
+    if not np.all(_orient(xy, tri) > 0):
+        raise ValueError("perturbation flipped a triangle")
+    return build_halfedges(tri, xy, name=f"near_tie_delaunay_{n_points}_{side}_s{seed}")
+
+
 def two_triangle_square() -> HalfEdgeMesh:
     """The two triangles of a unit square cut by a diagonal (paper Fig. 3):
     the diagonal is the shared longest edge, so the result is one 4-gon."""

@@ -50,16 +50,21 @@ def assert_parity(mesh, g: dict, r) -> None:
     T = mesh.n_triangles
     le, f0, f1, seed = oracle_labels(mesh, r)
     assert np.array_equal(g["le"], le), f"stage 1 longest edge: {np.count_nonzero(g['le'] != le)} triangles differ"
-    gf1 = np.stack([(g["flags"] >> k) & 1 for k in range(3)], axis=1)
-    gf0 = np.stack([(g["flags"] >> (3 + k)) & 1 for k in range(3)], axis=1)
+    gf1 = np.stack([(g["flags"] >> k) & 1 for k in range(3)], axis=1).astype(np.uint8)
     gseed = (g["flags"] >> 6) & 1
-    assert np.array_equal(gf0, f0), "stage 2 frontier labels differ"
-    assert np.array_equal(gseed, seed), "stage 3 seeds differ"
     # tips: the same set of (frontier half-edge, chord) pairs, any order
     gp = sorted(zip(g["tips"].tolist(), g["chords"].tolist()))
     op = sorted(zip(r.tip_out.tolist(), r.chord.tolist()))
     assert gp == op, f"stage 5a tips/chords differ ({len(gp)} vs {len(op)})"
     assert np.array_equal(gf1, f1), "stage 5a frontier after repair differs"
+    # stage 2: F0 = F1 without the chord half-edges
+    gf0 = gf1.reshape(-1).copy()
+    if len(g["chords"]):
+        gf0[g["chords"]] = 0
+        gf0[mesh.twin[g["chords"]]] = 0
+    assert np.array_equal(gf0.reshape(T, 3), f0), "stage 2 frontier labels differ"
+    assert np.array_equal(gseed, seed), "stage 3 seeds differ"
+    assert not np.any(g["flags"] & 0x38), "flag bits 3-5 are reserved (zero)"
     assert np.array_equal(g["next"], r.next_out), f"next differs at {np.count_nonzero(g['next'] != r.next_out)} half-edges"
     assert np.array_equal(g["prev"], r.prev_out), f"prev differs at {np.count_nonzero(g['prev'] != r.prev_out)} half-edges"
     assert g["n_polygons"] == r.n_polygons, f"P {g['n_polygons']} vs {r.n_polygons}"

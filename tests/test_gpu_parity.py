@@ -36,6 +36,15 @@ def _lattice(seed):
     raise AssertionError("no lattice mesh")
 
 
+def _near_tie(seed):
+    for s in range(seed, seed + 10):
+        try:
+            return meshgen.near_tie_delaunay(3000, 60, seed=s)
+        except ValueError:
+            continue
+    raise AssertionError("no near-tie mesh")
+
+
 SMALL = [
     meshgen.two_triangle_square,
     lambda: meshgen.from_triangles([[0, 1, 2]], [[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]], name="one_triangle"),
@@ -49,6 +58,8 @@ SMALL = [
     lambda: meshgen.random_delaunay(30_000, seed=7),
     lambda: _lattice(200),                                # exact ties everywhere
     lambda: _lattice(300),
+    lambda: _near_tie(0),                                 # lengths equal up to a few ulps
+    lambda: _near_tie(1),
 ]
 
 
