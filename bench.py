@@ -187,18 +187,23 @@ def ncu_traffic(kernel: str):
 
 
 def algorithmic_bytes(T, V, NF, P):
-    """Bytes the method must move once (next/prev of interior half-edges are
-    implicit in the layout; label bytes are L2-resident and not counted):
-    origin 12T + twin 12T + coords 16V + next/prev of frontier half-edges
-    8 N_F + CSR he_list/v_list 8 N_F + seeds/offsets 8P."""
+    """Bytes the method must move once, B_alg = 24T + 16V + 16 N_F + 8P
+    (next/prev of interior half-edges are implicit in the layout; label
+    bytes are L2-resident and not counted), and per kernel the bytes that
+    kernel must move for its own job (its unique inputs and outputs; the
+    output kernels re-read next, so the per-kernel figures sum to more
+    than B_alg)."""
+    total = 24 * T + 16 * V + 16 * NF + 8 * P
     per_stage = {
-        "longest_edge": 12 * T + 16 * V,          # origin + coords
-        "label_relink": 12 * T + 8 * NF,          # twin + next/prev writes
+        "longest_edge": 12 * T + 16 * V + T,        # origin, coords; le out
+        "label_relink": 12 * T + T + 8 * NF + T,    # twin, le; next/prev of frontier, flags out
         "chords": 0,
         "chord_links": 0,
-        "polygons": 8 * NF + 8 * P + 4,           # he_list, v_list, seeds, offsets
+        "poly_count": 4 * NF + T + 4 * P,           # next of frontier, flags; minima out
+        "tile_scan": 0,
+        "poly_emit": 4 * NF + 4 * NF + 4 * P + 8 * NF + 8 * P,  # next, origin, minima; CSR out
     }
-    return sum(per_stage.values()), per_stage
+    return total, per_stage
 
 
 # ---------------------------------------------------------------------------

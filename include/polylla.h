@@ -153,8 +153,11 @@ const char *polylla_status_string(int status);
  *                 half-edge 3t+k (stage 1);
  *   flags [T] uint8: bits 0-2 frontier after repair (F1) of 3t+k (the
  *                 stage-2 frontier F0 is F1 without the chord half-edges),
- *                 bits 3-5 zero, bit 6 set when the triangle's longest
- *                 half-edge is the seed of its terminal-edge region (stage 3);
+ *                 bits 3-5 walk-start marks: set on every frontier
+ *                 half-edge that may be the smallest of its polygon (a
+ *                 superset of the seeds), bit 6 set when the triangle's
+ *                 longest half-edge is the seed of its terminal-edge region
+ *                 (stage 3);
  *   tips [n_tips] int32: for each barrier tip, the stage-2 frontier
  *                 half-edge leaving it (order unspecified);
  *   chords [n_tips] int32: the chord half-edge leaving the same tip.

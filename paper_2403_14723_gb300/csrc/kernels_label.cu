@@ -159,62 +159,65 @@ __device__ __forceinline__ uint32_t longest_of(double2 p0, double2 p1, double2 p
     return k;
 }
 
-// Persistent CTAs walk 1024-triangle tiles.  The origin triples of the next
-// tile are bulk-copied (TMA engine, cp.async.bulk + mbarrier) into the other
-// half of a two-stage shared-memory ring while the current tile computes, so
-// the HBM stream of origin never waits on the coordinate gathers.  Each
-// thread takes 4 triangles (strided by 256, so a warp's gathers and byte
-// stores stay contiguous) and issues their 12 coordinate loads together.
+// Persistent warps walk 64-triangle tiles.  Each warp owns a two-stage
+// shared-memory ring: lane 0 bulk-copies (TMA engine, cp.async.bulk +
+// mbarrier) the origin triples of the warp's next tile while the warp
+// computes the current one, so the HBM stream of origin never waits on the
+// coordinate gathers and no warp waits for another (no block barrier).
+// Each lane takes 2 triangles (lane and lane + 32, so a warp's gathers and
+// byte stores stay contiguous) and issues their 6 coordinate loads together.
 __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w) {
-    __shared__ __align__(128) int32_t s_org[2][3 * LE_TILE];
-    __shared__ __align__(8) uint64_t s_bar[2];
-    // reset this generate's control block and scan look-back words
+    constexpr int NW = LE_THREADS / 32;
+    __shared__ __align__(128) int32_t s_org[NW][2][3 * LE_TILE];
+    __shared__ __align__(8) uint64_t s_bar[NW][2];
+    // reset this generate's control block (error word, tip count, totals)
     const int32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t gsz = gridDim.x * blockDim.x;
-    for (int32_t i = gtid; i < w.n_tiles; i += gsz) w.tile_status[i] = 0ull;
     if (gtid < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[gtid] = 0;
 
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;
-    if (threadIdx.x == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
+    uint64_t *bar = s_bar[warp];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    // the copy may round the tail up to 16 bytes: at most 3 ints past 3T,
+    __syncwarp();
+    // the copy rounds the tail up to 16 bytes: at most 3 ints past 3T,
     // inside origin because H >= 3T + 3 (checked at create)
     auto issue = [&](int32_t tile, int st) {
         const int32_t t0 = tile * LE_TILE;
         const int32_t nt = min(LE_TILE, m.T - t0);
         const uint32_t bytes = ((uint32_t)(12 * nt) + 15u) & ~15u;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&s_bar[st], bytes);
-        bulk_load(s_org[st], m.origin + 3 * (int64_t)t0, bytes, &s_bar[st]);
+        mbar_arrive_expect_tx(&bar[st], bytes);
+        bulk_load(s_org[warp][st], m.origin + 3 * (int64_t)t0, bytes, &bar[st]);
     };
-    int32_t tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < n_tiles) issue(tile, 0);
+    const int32_t nwarps = gridDim.x * NW;
+    int32_t tile = blockIdx.x * NW + warp;
+    if (lane == 0 && tile < n_tiles) issue(tile, 0);
     uint32_t parity = 0u;  // bit st = parity to wait for on stage st
-    constexpr int PER = LE_TILE / LE_THREADS;
-    for (int it = 0; tile < n_tiles; it++, tile += gridDim.x) {
+    constexpr int PER = LE_TILE / 32;
+    for (int it = 0; tile < n_tiles; it++, tile += nwarps) {
         const int st = it & 1;
-        const int32_t nxt = tile + gridDim.x;
-        if (threadIdx.x == 0 && nxt < n_tiles) issue(nxt, st ^ 1);
-        const bool ok = mbar_wait(&s_bar[st], (parity >> st) & 1u);
-        if (__syncthreads_or(!ok)) {
-            // give up: record it, wait (bounded) for this block's copies in
-            // flight so no bulk copy lands after the block has left, return
-            if (threadIdx.x == 0) atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
-            mbar_wait(&s_bar[st], (parity >> st) & 1u);
-            if (nxt < n_tiles) mbar_wait(&s_bar[st ^ 1], (parity >> (st ^ 1)) & 1u);
+        const int32_t nxt = tile + nwarps;
+        if (lane == 0 && nxt < n_tiles) issue(nxt, st ^ 1);
+        const bool ok = mbar_wait(&bar[st], (parity >> st) & 1u);
+        if (__any_sync(0xffffffffu, !ok)) {
+            // give up: record it, wait (bounded) for this warp's copies in
+            // flight so no bulk copy lands after the warp has left, return
+            if (lane == 0) atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
+            mbar_wait(&bar[st], (parity >> st) & 1u);
+            if (nxt < n_tiles) mbar_wait(&bar[st ^ 1], (parity >> (st ^ 1)) & 1u);
             return;
         }
         parity ^= 1u << st;
         const int32_t t0 = tile * LE_TILE;
-        const int32_t *so = s_org[st];
+        const int32_t *so = s_org[warp][st];
         double2 p[PER][3];
 #pragma unroll
         for (int q = 0; q < PER; q++) {
-            const int32_t lt = threadIdx.x + q * LE_THREADS;
+            const int32_t lt = lane + 32 * q;
             if (t0 + lt < m.T) {
                 p[q][0] = __ldg(m.xy + so[3 * lt]);
                 p[q][1] = __ldg(m.xy + so[3 * lt + 1]);
@@ -223,11 +226,11 @@ __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w)
         }
 #pragma unroll
         for (int q = 0; q < PER; q++) {
-            const int32_t lt = threadIdx.x + q * LE_THREADS;
+            const int32_t lt = lane + 32 * q;
             const int32_t t = t0 + lt;
             if (t < m.T) w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t, m.twin);
         }
-        __syncthreads();  // stage st is refilled next iteration
+        __syncwarp();  // stage st is refilled next iteration
     }
 }
 
@@ -239,9 +242,9 @@ int longest_edge_blocks_per_sm() {
 
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
     const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;
-    int blocks = n_tiles < w.le_blocks ? n_tiles : w.le_blocks;
-    // the control-block reset needs >= 8 threads and covers the look-back
-    // words with a grid-stride loop, so any grid >= 1 works
+    const int32_t want = (n_tiles + LE_THREADS / 32 - 1) / (LE_THREADS / 32);  // one tile per warp
+    const int blocks = want < w.le_blocks ? want : w.le_blocks;
+    // the control-block reset needs >= 8 threads: any grid >= 1 works
     k_longest_edge<<<blocks, LE_THREADS, 0, s>>>(m, w);
 }
 
@@ -264,6 +267,8 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 // rotation loads anyway, so the twin array is read from HBM once and no
 // frontier array is needed.  Twin values are split into (triangle, corner)
 // once, so a rotation step costs one twin and one byte load.
+// next and prev of the block are assembled in shared memory and stored
+// coalesced; only prev[x] for an x outside the block is stored directly.
 // In place is race-free: the rotation reads only twin and le; each next[e]
 // is written by e's own thread and each prev[x] by the unique e with
 // next[e] = x (or by x's own thread when x is not frontier).
@@ -271,71 +276,116 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 __device__ __forceinline__ int32_t div3(int32_t x) { return x / 3; }
 
 __global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w) {
-    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.T) return;
-    const int32_t HI = 3 * m.T;
-    const int32_t e0 = 3 * t;
-    int32_t tw[3], ttri[3];
-    uint32_t tloc[3], lnb[3];
-    tw[0] = __ldg(m.twin + e0);
-    tw[1] = __ldg(m.twin + e0 + 1);
-    tw[2] = __ldg(m.twin + e0 + 2);
-    const uint32_t lt = w.le[t];
-    uint32_t F = 0, twle = 0;
+    // next and prev of the block's 3*256 half-edges, stored coalesced at the
+    // end; prev entries whose predecessor lies outside the block stay -1
+    // here and are stored directly by that predecessor's thread
+    __shared__ __align__(16) int32_t s_nx[3 * RL_THREADS];
+    __shared__ __align__(16) int32_t s_pv[3 * RL_THREADS];
+    const int32_t t0 = blockIdx.x * RL_THREADS;
+    const int32_t nT = min(RL_THREADS, m.T - t0);
+    const int32_t eb = 3 * t0;  // 3072-byte aligned
+    const int32_t nE = 3 * nT;
+    for (int i = threadIdx.x; i < nE; i += RL_THREADS) s_pv[i] = -1;
+    __syncthreads();
+    const int32_t t = t0 + threadIdx.x;
+    uint32_t fl = 0;  // the triangle's flags byte, completed after the block's links are known
+    if (threadIdx.x < nT) {
+        const int32_t HI = 3 * m.T;
+        const int32_t e0 = 3 * t;
+        int32_t tw[3], ttri[3];
+        uint32_t tloc[3], lnb[3];
+        tw[0] = __ldg(m.twin + e0);
+        tw[1] = __ldg(m.twin + e0 + 1);
+        tw[2] = __ldg(m.twin + e0 + 2);
+        const uint32_t lt = w.le[t];
+        uint32_t F = 0, twle = 0;
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const bool b = tw[k] >= HI;
-        ttri[k] = div3(tw[k]);
-        tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
-        lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
-        const bool tl = !b && lnb[k] == tloc[k];
-        F |= (uint32_t)(b || ((uint32_t)k != lt && !tl)) << k;
-        twle |= (uint32_t)tl << k;
-    }
-    const int32_t twl = lt == 0u ? tw[0] : (lt == 1u ? tw[1] : tw[2]);
-    const bool seed = (twl >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < twl);
-    w.flags[t] = (uint8_t)(F | ((uint32_t)seed << 6));
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const int32_t e = e0 + k;
-        const int j = k == 2 ? 0 : k + 1;
-        if (!((F >> k) & 1u)) {
-            m.next[e] = e0 + j;
-            m.prev[e] = e0 + (k == 0 ? 2 : k - 1);
-            continue;
+        for (int k = 0; k < 3; k++) {
+            const bool b = tw[k] >= HI;
+            ttri[k] = div3(tw[k]);
+            tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
+            lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
+            const bool tl = !b && lnb[k] == tloc[k];
+            F |= (uint32_t)(b || ((uint32_t)k != lt && !tl)) << k;
+            twle |= (uint32_t)tl << k;
         }
-        int32_t x = e0 + j;
-        if (!((F >> j) & 1u)) {
-            // cross the non-frontier edge x into the neighbouring triangle
-            int32_t ty = ttri[j];      // twin of x, interior: non-frontier is not border
-            uint32_t ly = tloc[j];
-            uint32_t ley = lnb[j];     // le of tri(y)
-            int32_t steps = 0;
-            while (true) {
-                const uint32_t lx = ly == 2u ? 0u : ly + 1u;
-                x = 3 * ty + (int32_t)lx;               // next(y), in tri(y)
-                const int32_t tx = __ldg(m.twin + x);
-                if (tx >= HI) break;                     // border edge: frontier
-                const int32_t ttx = div3(tx);
-                const uint32_t ltx = (uint32_t)(tx - 3 * ttx);
-                const uint32_t lex = w.le[ttx];
-                if (ley != lx && lex != ltx) break;      // neither half longest: frontier
-                ty = ttx;
-                ly = ltx;
-                ley = lex;
-                if (++steps > w.max_rot) {
-                    atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
-                    break;
+        const int32_t twl = lt == 0u ? tw[0] : (lt == 1u ? tw[1] : tw[2]);
+        const bool seed = (twl >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < twl);
+        fl = F | ((uint32_t)seed << 6);
+        const int32_t lb = 3 * (int32_t)threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int32_t e = e0 + k;
+            const int j = k == 2 ? 0 : k + 1;
+            if (!((F >> k) & 1u)) {
+                s_nx[lb + k] = e0 + j;
+                s_pv[lb + k] = e0 + (k == 0 ? 2 : k - 1);
+                continue;
+            }
+            int32_t x = e0 + j;
+            if (!((F >> j) & 1u)) {
+                // cross the non-frontier edge x into the neighbouring triangle
+                int32_t ty = ttri[j];      // twin of x, interior: non-frontier is not border
+                uint32_t ly = tloc[j];
+                uint32_t ley = lnb[j];     // le of tri(y)
+                int32_t steps = 0;
+                while (true) {
+                    const uint32_t lx = ly == 2u ? 0u : ly + 1u;
+                    x = 3 * ty + (int32_t)lx;               // next(y), in tri(y)
+                    const int32_t tx = __ldg(m.twin + x);
+                    if (tx >= HI) break;                     // border edge: frontier
+                    const int32_t ttx = div3(tx);
+                    const uint32_t ltx = (uint32_t)(tx - 3 * ttx);
+                    const uint32_t lex = w.le[ttx];
+                    if (ley != lx && lex != ltx) break;      // neither half longest: frontier
+                    ty = ttx;
+                    ly = ltx;
+                    ley = lex;
+                    if (++steps > w.max_rot) {
+                        atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
+                        break;
+                    }
                 }
             }
+            s_nx[lb + k] = x;
+            const uint32_t dx = (uint32_t)(x - eb);
+            if (dx < (uint32_t)nE) s_pv[dx] = e;
+            else m.prev[x] = e;
+            if (x == tw[k]) {
+                const int32_t slot = atomicAdd(&w.ctrl->n_tips, 1);
+                if (slot < w.tip_cap) w.tips[slot] = tw[k];
+                else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+            }
         }
-        m.next[e] = x;
-        m.prev[x] = e;
-        if (x == tw[k]) {
-            const int32_t slot = atomicAdd(&w.ctrl->n_tips, 1);
-            if (slot < w.tip_cap) w.tips[slot] = tw[k];
-            else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+    }
+    __syncthreads();
+    // Walk-start marks: a frontier half-edge can be its polygon's minimum
+    // only if next[e] > e and prev[e] > e.  prev[e] is known here when its
+    // predecessor lies in this block; otherwise (about 7% of frontier
+    // half-edges on the workloads measured) the mark is set whenever
+    // next[e] > e, which keeps the marks a superset of the minima.
+    if (threadIdx.x < nT) {
+        const int32_t lb = 3 * (int32_t)threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int32_t e = 3 * t + k;
+            const int32_t pv = s_pv[lb + k];
+            if (((fl >> k) & 1u) && s_nx[lb + k] > e && (pv < 0 || pv > e)) fl |= 8u << k;
         }
+        w.flags[t] = (uint8_t)fl;
+    }
+    int4 *dn = reinterpret_cast<int4 *>(m.next + eb);
+    for (int i = threadIdx.x; 4 * i < nE; i += RL_THREADS) {
+        if (4 * i + 3 < nE) {
+            dn[i] = reinterpret_cast<const int4 *>(s_nx)[i];
+        } else {
+            for (int q = 0; q < 4; q++)
+                if (4 * i + q < nE) m.next[eb + 4 * i + q] = s_nx[4 * i + q];
+        }
+    }
+    for (int i = threadIdx.x; i < nE; i += RL_THREADS) {
+        const int32_t v = s_pv[i];
+        if (v >= 0) m.prev[eb + i] = v;
     }
 }
 

@@ -16,8 +16,9 @@ __device__ __forceinline__ void set_flag_bit(uint8_t *flags, int32_t e, int shif
     unsigned int *word = reinterpret_cast<unsigned int *>(flags) + (t >> 2);
     atomicOr(word, 1u << (8 * (t & 3) + shift + loc_of(e)));
 }
-// F1 bit (bits 0-2) of half-edge e
+// F1 bit (bits 0-2) and walk-start mark (bits 3-5) of half-edge e
 __device__ __forceinline__ void set_f1(uint8_t *flags, int32_t e) { set_flag_bit(flags, e, 0); }
+__device__ __forceinline__ void set_start(uint8_t *flags, int32_t e) { set_flag_bit(flags, e, 3); }
 
 // ===========================================================================
 // Chords (Algorithm 6 first part / Algorithm 11).  For the tip b left by
@@ -69,6 +70,8 @@ void launch_chords(const MeshView &m, const Work &w, cudaStream_t s) {
 //             twin(prev z)) -> next[twin z] = c
 // Every other link keeps its stage-4 value.  Two chords at one vertex write
 // the link between them with the same value, so no ordering is needed.
+// Every half-edge whose next or prev changes gets the walk-start mark (the
+// polygon kernel needs the marks to be a superset of the polygon minima).
 // ===========================================================================
 __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, int32_t c, int32_t HI) {
     // clockwise neighbour
@@ -81,6 +84,8 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
     }
     m.next[tc] = y;
     m.prev[y] = tc;
+    set_start(w.flags, tc);
+    set_start(w.flags, y);
     // counter-clockwise neighbour; reaching a border half-edge z means the
     // interior half-edge before it, pv, is twin(z)
     int32_t pv = pv_of(c);
@@ -94,6 +99,8 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
     // twin(z) == pv
     m.next[pv] = c;
     m.prev[c] = pv;
+    set_start(w.flags, pv);
+    set_start(w.flags, c);
 }
 
 __global__ void __launch_bounds__(256) k_chord_links(MeshView m, Work w) {

@@ -12,9 +12,9 @@ using namespace polylla;
 
 namespace {
 
-constexpr int kStages = 5;
+constexpr int kStages = 7;
 const char *kStageNames[kStages] = {
-    "longest_edge", "label_relink", "chords", "chord_links", "polygons",
+    "longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan", "poly_emit",
 };
 
 }  // namespace
@@ -95,6 +95,10 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.n_tiles = (int32_t)((HI + POLY_TILE - 1) / POLY_TILE);
     if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tiles))) return rc;
     c->w.tile_status = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tiles))) return rc;
+    c->w.tile_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)c->w.n_tiles * POLY_TILE))) return rc;
+    c->w.mins = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)T))) return rc;
     c->w.seeds = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(T + 1)))) return rc;
@@ -223,7 +227,8 @@ int polylla_generate(polylla_ctx *c, polylla_stream stream) {
     c->launches = 0;
     if (c->timing) CK(cudaEventRecord(c->ev[0], s));
     void (*stages[kStages])(const MeshView &, const Work &, cudaStream_t) = {
-        launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links, launch_polygons,
+        launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links,
+        launch_poly_count, launch_tile_scan, launch_poly_emit,
     };
     for (int i = 0; i < kStages; i++) {
         stages[i](c->mesh, c->w, s);

@@ -7,7 +7,10 @@
 //                        bit 6 the triangle's longest half-edge is a seed
 //   tips    [V]   int32  F0 half-edge leaving each barrier tip
 //   chords  [V]   int32  chord half-edge leaving each barrier tip
-//   tile_status [n_tiles] u64  look-back words of the polygon scan
+//   tile_status [n_tiles] u64  (polygon count, length) of each 2048-half-edge tile
+//   tile_pre    [n_tiles] u64  exclusive prefix of tile_status
+//   mins  [n_tiles*2048] int32  per tile, its polygon minima in order:
+//                        tile-local index | length << 11
 //   seeds [T], offsets [T+1], he_list [3T], v_list [3T]   CSR output
 //   ctrl          DevCtrl       counters and the device error word
 #pragma once
@@ -27,7 +30,7 @@ enum : int32_t {
 struct DevCtrl {
     int32_t error;       // OR of DEV_ERR_* bits of this generate
     int32_t n_tips;      // barrier tips found by the relink
-    int32_t ticket;      // next tile of the polygon kernel
+    int32_t spare;
     int32_t n_polygons;  // P, written by the last polygon tile
     int32_t n_frontier;  // N_F, written by the last polygon tile
     int32_t pad[3];
@@ -49,6 +52,8 @@ struct Work {
     int32_t *chords;
     int32_t tip_cap;
     unsigned long long *tile_status;
+    unsigned long long *tile_pre;
+    int32_t *mins;
     int32_t n_tiles;
     int32_t *seeds;
     int32_t *offsets;
@@ -62,15 +67,18 @@ struct Work {
 
 // polygon kernel tiling: 2048 consecutive half-edges per 256-thread block;
 // the tile's CSR output is staged in shared memory up to POLY_BUF entries
-constexpr int POLY_THREADS = 256;
+#ifndef POLYLLA_POLY_THREADS
+#define POLYLLA_POLY_THREADS 256
+#endif
+constexpr int POLY_THREADS = POLYLLA_POLY_THREADS;
 constexpr int POLY_ITEMS = 8;
 constexpr int POLY_TILE = POLY_THREADS * POLY_ITEMS;
-constexpr int POLY_BUF = 1024;
+constexpr int POLY_BUF = POLY_TILE / 2;
 
-// longest-edge kernel: persistent CTAs, 512-triangle tiles of origin
-// bulk-copied (TMA) into a two-stage shared-memory ring
+// longest-edge kernel: persistent warps, each with a two-stage ring of
+// 64-triangle tiles of origin bulk-copied (TMA) into shared memory
 constexpr int LE_THREADS = 256;
-constexpr int LE_TILE = 512;
+constexpr int LE_TILE = 64;
 
 // relink kernel: one thread per triangle
 constexpr int RL_THREADS = 256;
@@ -142,7 +150,9 @@ int longest_edge_blocks_per_sm();
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chords(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_polygons(const MeshView &m, const Work &w, cudaStream_t s);
-int polygons_configure();  // opt in to the polygon kernel's dynamic shared memory
+void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_poly_emit(const MeshView &m, const Work &w, cudaStream_t s);
+int polygons_configure();  // opt in to the emit kernel's dynamic shared memory
 
 }  // namespace polylla

@@ -64,7 +64,10 @@ def assert_parity(mesh, g: dict, r) -> None:
         gf0[mesh.twin[g["chords"]]] = 0
     assert np.array_equal(gf0.reshape(T, 3), f0), "stage 2 frontier labels differ"
     assert np.array_equal(gseed, seed), "stage 3 seeds differ"
-    assert not np.any(g["flags"] & 0x38), "flag bits 3-5 are reserved (zero)"
+    # walk-start marks: only on frontier half-edges, and on every polygon seed
+    gmark = np.stack([(g["flags"] >> (3 + k)) & 1 for k in range(3)], axis=1).reshape(-1).astype(bool)
+    assert not np.any(gmark & ~gf1.reshape(-1).astype(bool)), "walk-start mark on a non-frontier half-edge"
+    assert np.all(gmark[r.seeds]), "a polygon seed has no walk-start mark"
     assert np.array_equal(g["next"], r.next_out), f"next differs at {np.count_nonzero(g['next'] != r.next_out)} half-edges"
     assert np.array_equal(g["prev"], r.prev_out), f"prev differs at {np.count_nonzero(g['prev'] != r.prev_out)} half-edges"
     assert g["n_polygons"] == r.n_polygons, f"P {g['n_polygons']} vs {r.n_polygons}"

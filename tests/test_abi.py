@@ -47,9 +47,10 @@ def test_status_strings_without_gpu(lib_path):
     lib = polylla.load_library()
     assert lib.polylla_status_string(0) == b"ok"
     assert lib.polylla_status_string(-2) == b"invalid mesh layout"
-    assert lib.polylla_stage_count() == 5
-    names = [lib.polylla_stage_name(i).decode() for i in range(5)]
-    assert names == ["longest_edge", "label_relink", "chords", "chord_links", "polygons"]
+    assert lib.polylla_stage_count() == 7
+    names = [lib.polylla_stage_name(i).decode() for i in range(7)]
+    assert names == ["longest_edge", "label_relink", "chords", "chord_links",
+                     "poly_count", "tile_scan", "poly_emit"]
 
 
 def test_null_arguments_rejected_without_gpu(lib_path):
