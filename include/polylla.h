@@ -46,7 +46,8 @@ enum polylla_status {
     POLYLLA_ERR_CUDA = -4,             /* any other CUDA error (see polylla_cuda_error) */
     POLYLLA_ERR_NONTERMINATING = -5,   /* a rotation or cycle walk hit its cap       */
     POLYLLA_ERR_CAPACITY = -6,         /* an internal list overflowed its capacity   */
-    POLYLLA_ERR_TIMEOUT = -7,          /* a device wait gave up (scan look-back)     */
+    POLYLLA_ERR_TIMEOUT = -7,          /* a device wait gave up                      */
+    POLYLLA_ERR_TOO_LARGE = -8,        /* mesh exceeds polylla_generate_noalloc's scratch */
 };
 
 /* Input mesh (device arrays owned by the caller). */
@@ -210,6 +211,43 @@ int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
 int polylla_stage_count(void);
 const char *polylla_stage_name(int32_t i);
 int polylla_launch_count(polylla_ctx *ctx);
+
+/*
+ * polylla_generate_noalloc -- the whole method, allocating nothing.
+ *
+ * (No counterpart in the paper: this is a deployment convenience.)  For
+ * callers that cannot call cudaMalloc -- a serving loop that must not
+ * allocate once running, code recorded into a CUDA graph, or a process
+ * whose device memory belongs to another allocator.  It runs the same
+ * kernels as polylla_generate, but their scratch (labels, tip lists, tile
+ * totals, polygon minima, counters) lives in one static device array of
+ * fixed size that every GPU loading the library holds until the process
+ * exits (about 3 MB), so no context, no cudaMalloc and no cudaFree.
+ *
+ *   mesh    device arrays as for polylla_create; must satisfy the layout
+ *           polylla_create checks (no check is made here);
+ *           next/prev of [0, 3T) are rewritten as by polylla_generate.
+ *   seeds, offsets, he_list, v_list
+ *           caller-owned device outputs with capacities T, T+1, 3T, 3T.
+ *   status3 caller-owned device int32[3]: receives P, N_F and the device
+ *           error bits of this call (0 = success; 1 a rotation or walk hit
+ *           its cap, 2 a capacity was exceeded, 4 a wait gave up).
+ *   stream  everything is enqueued on it; the call does not synchronize.
+ * Returns POLYLLA_ERR_TOO_LARGE (nothing launched) when T exceeds
+ * POLYLLA_NOALLOC_MAX_TRIANGLES or V exceeds it by more than 2,
+ * POLYLLA_ERR_INVALID_ARGUMENT for NULL or misaligned pointers, otherwise
+ * POLYLLA_OK or POLYLLA_ERR_CUDA.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and it keeps the last call's contents:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.
+ */
+#define POLYLLA_NOALLOC_MAX_TRIANGLES 131072
+int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds, int32_t *offsets,
+                             int32_t *he_list, int32_t *v_list, int32_t *status3,
+                             polylla_stream stream);
 
 #ifdef __cplusplus
 }

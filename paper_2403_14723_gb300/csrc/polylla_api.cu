@@ -150,6 +150,7 @@ const char *polylla_status_string(int status) {
         case POLYLLA_ERR_NONTERMINATING: return "rotation or cycle walk did not terminate";
         case POLYLLA_ERR_CAPACITY: return "internal list capacity exceeded";
         case POLYLLA_ERR_TIMEOUT: return "device wait timed out";
+        case POLYLLA_ERR_TOO_LARGE: return "mesh larger than the no-allocation scratch";
         default: return "unknown status";
     }
 }

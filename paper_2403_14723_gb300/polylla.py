@@ -19,7 +19,9 @@ STATUS = {
     0: "ok", -1: "invalid argument", -2: "invalid mesh layout", -3: "out of device memory",
     -4: "CUDA error", -5: "rotation or cycle walk did not terminate",
     -6: "internal list capacity exceeded", -7: "device wait timed out",
+    -8: "mesh larger than the no-allocation scratch",
 }
+POLYLLA_NOALLOC_MAX_TRIANGLES = 131072
 
 
 class PolyllaError(RuntimeError):
@@ -86,6 +88,9 @@ _SIGNATURES = {
     "polylla_stage_count": (ctypes.c_int, []),
     "polylla_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "polylla_launch_count": (ctypes.c_int, [ctypes.c_void_p]),
+    "polylla_generate_noalloc": (ctypes.c_int, [ctypes.POINTER(polylla_mesh), ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
 }
 
 _lib = None
@@ -293,6 +298,28 @@ def polylla_generate_host(ctx: int, host_in: dict, host_out: dict, validate: boo
     _check(lib.polylla_generate_host(ctypes.c_void_p(ctx), ctypes.byref(hm), ctypes.byref(hr),
                                      1 if validate else 0, _stream_ptr(stream)), "polylla_generate_host")
     return hr.n_polygons, hr.n_frontier
+
+
+def polylla_generate_noalloc(mesh: DeviceMesh, seeds, offsets, he_list, v_list, status3, stream=None) -> None:
+    """The whole method with no allocation in the library: the caller
+    passes device tensors for the outputs (int32, capacities T, T+1, 3T, 3T)
+    and a device int32[3] that receives P, N_F and the device error bits.
+    Does not synchronize."""
+    import torch
+
+    lib = load_library()
+    V = mesh.coords.shape[0]
+    H = mesh.origin.numel()
+    T = int(mesh.n_triangles)
+    m = polylla_mesh(V, T, H,
+                     _dev_ptr(mesh.coords.view(-1), torch.float64, 2 * V),
+                     _dev_ptr(mesh.origin, torch.int32, H), _dev_ptr(mesh.twin, torch.int32, H),
+                     _dev_ptr(mesh.next, torch.int32, H), _dev_ptr(mesh.prev, torch.int32, H))
+    ptrs = [ctypes.c_void_p(t.data_ptr()) for t in (seeds, offsets, he_list, v_list, status3)]
+    for t, n in zip((seeds, offsets, he_list, v_list, status3), (T, T + 1, 3 * T, 3 * T, 3)):
+        if not t.is_cuda or t.dtype != torch.int32 or t.numel() < n:
+            raise ValueError(f"device int32 tensor of at least {n} elements expected")
+    _check(lib.polylla_generate_noalloc(ctypes.byref(m), *ptrs, _stream_ptr(stream)), "polylla_generate_noalloc")
 
 
 class Polylla:
