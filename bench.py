@@ -199,9 +199,12 @@ def algorithmic_bytes(T, V, NF, P):
         "label_relink": 12 * T + T + 8 * NF + T,    # twin, le; next/prev of frontier, flags out
         "chords": 0,
         "chord_links": 0,
-        "poly_count": 4 * NF + T + 4 * P,           # next of frontier, flags; minima out
-        "tile_scan": 0,
-        "poly_emit": 4 * NF + 4 * NF + 4 * P + 8 * NF + 8 * P,  # next, origin, minima; CSR out
+        "cand_count": T,                             # flags
+        "cand_scan": 0,
+        "cand_write": T,                             # flags (starts out: ~P ints, not counted)
+        "walk": 4 * NF,                              # next of every frontier half-edge once
+        "chunk_scan": 0,
+        "emit": 4 * NF + 4 * NF + 8 * NF + 8 * P,    # next, origin; CSR out
     }
     return total, per_stage
 

@@ -222,7 +222,7 @@ int polylla_launch_count(polylla_ctx *ctx);
  * kernels as polylla_generate, but their scratch (labels, tip lists, tile
  * totals, polygon minima, counters) lives in one static device array of
  * fixed size that every GPU loading the library holds until the process
- * exits (about 3 MB), so no context, no cudaMalloc and no cudaFree.
+ * exits (about 4.5 MB), so no context, no cudaMalloc and no cudaFree.
  *
  *   mesh    device arrays as for polylla_create; must satisfy the layout
  *           polylla_create checks (no check is made here);

@@ -12,10 +12,12 @@ using namespace polylla;
 
 namespace {
 
-constexpr int kStages = 7;
+constexpr int kStages = 10;
 const char *kStageNames[kStages] = {
-    "longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan", "poly_emit",
+    "longest_edge", "label_relink", "chords", "chord_links", "cand_count",
+    "cand_scan", "cand_write", "walk", "chunk_scan", "emit",
 };
+constexpr int kKernels = 11;  // chunk_scan launches two kernels
 
 }  // namespace
 
@@ -92,13 +94,20 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.tips = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)V))) return rc;
     c->w.chords = (int32_t *)p;
-    c->w.n_tiles = (int32_t)((HI + POLY_TILE - 1) / POLY_TILE);
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tiles))) return rc;
-    c->w.tile_status = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tiles))) return rc;
-    c->w.tile_pre = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)c->w.n_tiles * POLY_TILE))) return rc;
-    c->w.mins = (int32_t *)p;
+    c->w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
+    c->w.n_chunk_max = (int32_t)((HI + CHUNK - 1) / CHUNK);
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_cc_blocks))) return rc;
+    c->w.blk_a = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_cc_blocks))) return rc;
+    c->w.blk_a_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_chunk_max))) return rc;
+    c->w.blk_b = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_chunk_max))) return rc;
+    c->w.blk_b_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)HI))) return rc;
+    c->w.cand = (int32_t *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)HI))) return rc;
+    c->w.res = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)T))) return rc;
     c->w.seeds = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(T + 1)))) return rc;
@@ -119,6 +128,8 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
     c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
+    c->w.walk_blocks = 8 * (sms > 0 ? sms : 1);
+    c->w.emit_blocks = 2 * (sms > 0 ? sms : 1);
     if (polygons_configure() != 0) return cuda_fail(c, cudaGetLastError());
     c->w.max_rot = (opt && opt->max_rotation > 0) ? opt->max_rotation : 4096;
     for (int i = 0; i <= kStages; i++) {
@@ -229,13 +240,14 @@ int polylla_generate(polylla_ctx *c, polylla_stream stream) {
     if (c->timing) CK(cudaEventRecord(c->ev[0], s));
     void (*stages[kStages])(const MeshView &, const Work &, cudaStream_t) = {
         launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links,
-        launch_poly_count, launch_tile_scan, launch_poly_emit,
+        launch_cand_count, launch_cand_scan, launch_cand_write, launch_walk,
+        launch_chunk_scan, launch_emit,
     };
     for (int i = 0; i < kStages; i++) {
         stages[i](c->mesh, c->w, s);
-        c->launches++;
         if (c->timing) CK(cudaEventRecord(c->ev[i + 1], s));
     }
+    c->launches = kKernels;
     CK(cudaGetLastError());
     return POLYLLA_OK;
 }

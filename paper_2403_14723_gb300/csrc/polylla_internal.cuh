@@ -7,10 +7,9 @@
 //                        bit 6 the triangle's longest half-edge is a seed
 //   tips    [V]   int32  F0 half-edge leaving each barrier tip
 //   chords  [V]   int32  chord half-edge leaving each barrier tip
-//   tile_status [n_tiles] u64  (polygon count, length) of each 2048-half-edge tile
-//   tile_pre    [n_tiles] u64  exclusive prefix of tile_status
-//   mins  [n_tiles*2048] int32  per tile, its polygon minima in order:
-//                        tile-local index | length << 11
+//   cand  [3T]    int32  walk starts (marked frontier half-edges), ascending
+//   res   [3T]    int32  polygon length of each start that is a minimum, else 0
+//   blk_a/blk_a_pre, blk_b/blk_b_pre  u64  block and chunk totals, scanned
 //   seeds [T], offsets [T+1], he_list [3T], v_list [3T]   CSR output
 //   ctrl          DevCtrl       counters and the device error word
 #pragma once
@@ -30,10 +29,13 @@ enum : int32_t {
 struct DevCtrl {
     int32_t error;       // OR of DEV_ERR_* bits of this generate
     int32_t n_tips;      // barrier tips found by the relink
-    int32_t spare;
-    int32_t n_polygons;  // P, written by the last polygon tile
-    int32_t n_frontier;  // N_F, written by the last polygon tile
-    int32_t pad[3];
+    int32_t n_polygons;  // P
+    int32_t n_frontier;  // N_F
+    int32_t n_cand;      // walk starts
+    int32_t n_chunks;    // 2048-start chunks
+    int32_t pad[2];
+    unsigned long long n_cand64;  // walk starts, as scanned
+    unsigned long long grand_b;   // (P << 32 | N_F), as scanned
 };
 
 struct MeshView {
@@ -51,10 +53,15 @@ struct Work {
     int32_t *tips;
     int32_t *chords;
     int32_t tip_cap;
-    unsigned long long *tile_status;
-    unsigned long long *tile_pre;
-    int32_t *mins;
-    int32_t n_tiles;
+    unsigned long long *blk_a;      // walk starts per block of CC_TRI triangles
+    unsigned long long *blk_a_pre;  // their exclusive prefix
+    int32_t *cand;                  // walk starts in index order [3T]
+    int32_t *res;                   // polygon length per start, 0 if not a minimum [3T]
+    unsigned long long *blk_b;      // (minimum count, length) per CHUNK starts
+    unsigned long long *blk_b_pre;  // their exclusive prefix
+    int32_t n_cc_blocks;            // ceil(T / CC_TRI)
+    int32_t n_chunk_max;            // ceil(3T / CHUNK)
+    int32_t walk_blocks, emit_blocks;
     int32_t *seeds;
     int32_t *offsets;
     int32_t *he_list;
@@ -65,15 +72,16 @@ struct Work {
     int32_t le_blocks;           // grid of the persistent longest-edge kernel
 };
 
-// polygon kernel tiling: 2048 consecutive half-edges per 256-thread block;
-// the tile's CSR output is staged in shared memory up to POLY_BUF entries
-#ifndef POLYLLA_POLY_THREADS
-#define POLYLLA_POLY_THREADS 256
-#endif
-constexpr int POLY_THREADS = POLYLLA_POLY_THREADS;
-constexpr int POLY_ITEMS = 8;
-constexpr int POLY_TILE = POLY_THREADS * POLY_ITEMS;
-constexpr int POLY_BUF = POLY_TILE / 2;
+// output kernels: start counting/compaction over blocks of CC_TRI
+// triangles (16 per thread, one int4 of flags), walks and emission over
+// chunks of CHUNK starts, single-block scans of the block/chunk totals
+constexpr int CC_THREADS = 1024;
+constexpr int CC_PER = 16;
+constexpr int CC_TRI = CC_THREADS * CC_PER;
+constexpr int SCAN_THREADS = 1024;
+constexpr int CHUNK = 2048;
+constexpr int WALK_THREADS = 256;
+constexpr int EMIT_THREADS = 1024;
 
 // longest-edge kernel: persistent warps, each with a two-stage ring of
 // 64-triangle tiles of origin bulk-copied (TMA) into shared memory
@@ -150,9 +158,12 @@ int longest_edge_blocks_per_sm();
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chords(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_poly_emit(const MeshView &m, const Work &w, cudaStream_t s);
-int polygons_configure();  // opt in to the emit kernel's dynamic shared memory
+void launch_cand_count(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_cand_scan(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_cand_write(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_walk(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);  // two kernels
+void launch_emit(const MeshView &m, const Work &w, cudaStream_t s);
+int polygons_configure();
 
 }  // namespace polylla

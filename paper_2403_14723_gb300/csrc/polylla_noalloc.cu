@@ -22,7 +22,9 @@ namespace {
 constexpr int32_t NA_MAX_T = POLYLLA_NOALLOC_MAX_TRIANGLES;
 // a triangulated disk has V = (T + B + 2) / 2 with B <= T + 2 boundary edges
 constexpr int32_t NA_MAX_V = NA_MAX_T + 2;
-constexpr int64_t NA_MAX_TILES = (3 * (int64_t)NA_MAX_T + POLY_TILE - 1) / POLY_TILE;
+constexpr int64_t NA_MAX_HI = 3 * (int64_t)NA_MAX_T;
+constexpr int64_t NA_MAX_CC = ((int64_t)NA_MAX_T + CC_TRI - 1) / CC_TRI;
+constexpr int64_t NA_MAX_CHUNKS = (NA_MAX_HI + CHUNK - 1) / CHUNK;
 
 constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 // layout of the scratch array (byte offsets, each 256-aligned)
@@ -30,10 +32,13 @@ constexpr size_t OFF_LE = 0;
 constexpr size_t OFF_FLAGS = OFF_LE + up256(NA_MAX_T);
 constexpr size_t OFF_TIPS = OFF_FLAGS + up256(NA_MAX_T);
 constexpr size_t OFF_CHORDS = OFF_TIPS + up256(4 * (size_t)NA_MAX_V);
-constexpr size_t OFF_TILE_STATUS = OFF_CHORDS + up256(4 * (size_t)NA_MAX_V);
-constexpr size_t OFF_TILE_PRE = OFF_TILE_STATUS + up256(8 * (size_t)NA_MAX_TILES);
-constexpr size_t OFF_MINS = OFF_TILE_PRE + up256(8 * (size_t)NA_MAX_TILES);
-constexpr size_t OFF_CTRL = OFF_MINS + up256(4 * (size_t)NA_MAX_TILES * POLY_TILE);
+constexpr size_t OFF_BLK_A = OFF_CHORDS + up256(4 * (size_t)NA_MAX_V);
+constexpr size_t OFF_BLK_A_PRE = OFF_BLK_A + up256(8 * (size_t)NA_MAX_CC);
+constexpr size_t OFF_BLK_B = OFF_BLK_A_PRE + up256(8 * (size_t)NA_MAX_CC);
+constexpr size_t OFF_BLK_B_PRE = OFF_BLK_B + up256(8 * (size_t)NA_MAX_CHUNKS);
+constexpr size_t OFF_CAND = OFF_BLK_B_PRE + up256(8 * (size_t)NA_MAX_CHUNKS);
+constexpr size_t OFF_RES = OFF_CAND + up256(4 * (size_t)NA_MAX_HI);
+constexpr size_t OFF_CTRL = OFF_RES + up256(4 * (size_t)NA_MAX_HI);
 constexpr size_t NA_BYTES = OFF_CTRL + up256(sizeof(DevCtrl));
 
 constexpr int kMaxDevices = 64;
@@ -41,7 +46,7 @@ constexpr int kMaxDevices = 64;
 }  // namespace
 
 // The scratch.  Every GPU that loads the library holds it (NA_BYTES, about
-// 3 MB) until the process exits.  In host code its name is only a host-side
+// 4.5 MB) until the process exits.  In host code its name is only a host-side
 // stand-in: the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -100,10 +105,14 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.tips = reinterpret_cast<int32_t *>(base + OFF_TIPS);
     w.chords = reinterpret_cast<int32_t *>(base + OFF_CHORDS);
     w.tip_cap = V;
-    w.tile_status = reinterpret_cast<unsigned long long *>(base + OFF_TILE_STATUS);
-    w.tile_pre = reinterpret_cast<unsigned long long *>(base + OFF_TILE_PRE);
-    w.mins = reinterpret_cast<int32_t *>(base + OFF_MINS);
-    w.n_tiles = (int32_t)((3 * (int64_t)T + POLY_TILE - 1) / POLY_TILE);
+    w.blk_a = reinterpret_cast<unsigned long long *>(base + OFF_BLK_A);
+    w.blk_a_pre = reinterpret_cast<unsigned long long *>(base + OFF_BLK_A_PRE);
+    w.blk_b = reinterpret_cast<unsigned long long *>(base + OFF_BLK_B);
+    w.blk_b_pre = reinterpret_cast<unsigned long long *>(base + OFF_BLK_B_PRE);
+    w.cand = reinterpret_cast<int32_t *>(base + OFF_CAND);
+    w.res = reinterpret_cast<int32_t *>(base + OFF_RES);
+    w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
+    w.n_chunk_max = (int32_t)((3 * (int64_t)T + CHUNK - 1) / CHUNK);
     w.seeds = seeds;
     w.offsets = offsets;
     w.he_list = he_list;
@@ -112,17 +121,23 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.max_rot = 4096;
     w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
     w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
+    w.walk_blocks = 8 * (sms > 0 ? sms : 1);
+    w.emit_blocks = 2 * (sms > 0 ? sms : 1);
 
-    // The first kernel zeroes the control block; every other scratch word is
-    // written before it is read, so the previous call's contents never leak.
+    // The first kernel zeroes the control block and k_cand_count zeroes the
+    // chunk totals; every other scratch word is written before it is read,
+    // so the previous call's contents never leak into this one.
     cudaStream_t s = (cudaStream_t)stream;
     launch_longest_edge(m, w, s);
     launch_label_relink(m, w, s);
     launch_chords(m, w, s);
     launch_chord_links(m, w, s);
-    launch_poly_count(m, w, s);
-    launch_tile_scan(m, w, s);
-    launch_poly_emit(m, w, s);
+    launch_cand_count(m, w, s);
+    launch_cand_scan(m, w, s);
+    launch_cand_write(m, w, s);
+    launch_walk(m, w, s);
+    launch_chunk_scan(m, w, s);
+    launch_emit(m, w, s);
     // status3 = {P, N_F, device error bits}, copied device to device
     if (cudaMemcpyAsync(status3, &w.ctrl->n_polygons, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s) !=
             cudaSuccess ||
