@@ -251,7 +251,7 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 // ===========================================================================
 // Stages 2-4 fused: frontier labels (Algorithm 3 / 9), seeds (Algorithm 4 /
 // 10) and the relink of every frontier half-edge (Section 4.2; the per-half-
-// edge form of Algorithm 12), one thread per triangle.
+// edge form of Algorithm 12), one thread per triangle for the labels.
 //
 //   F0[e] = border(e) or (not LE[e] and not LE[twin e])
 //   seed  = the triangle's longest half-edge e when it is the smaller half of
@@ -266,34 +266,42 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 // longest-edge bytes (L2-resident) and that half-edge's twin, which the
 // rotation loads anyway, so the twin array is read from HBM once and no
 // frontier array is needed.  Twin values are split into (triangle, corner)
-// once, so a rotation step costs one twin and one byte load.
+// once, so a rotation step costs one twin and one byte load, and the next
+// step's twin is fetched together with the current step's byte.
 // next and prev of the block are assembled in shared memory and stored
 // coalesced; only prev[x] for an x outside the block is stored directly.
 // In place is race-free: the rotation reads only twin and le; each next[e]
-// is written by e's own thread and each prev[x] by the unique e with
-// next[e] = x (or by x's own thread when x is not frontier).
+// is written once (by e's thread, or by the lane that ran e's rotation) and
+// each prev[x] once, for the unique e with next[e] = x (or by x's own
+// thread when x is not frontier).
 // ===========================================================================
-__device__ __forceinline__ int32_t div3(int32_t x) { return x / 3; }
+__device__ __forceinline__ int32_t div3(int32_t x) { return (int32_t)((uint32_t)x / 3u); }
 
+// Rotations are compacted per warp.  Each thread labels its triangle and
+// links the frontier half-edges whose successor is the next half-edge of the
+// same triangle; the others (the successor lies across a non-frontier edge)
+// become tasks that the warp's lanes then take one each, so a warp runs its
+// rotations side by side instead of once per local half-edge.
 __global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w) {
-    // next and prev of the block's 3*256 half-edges, stored coalesced at the
-    // end; prev entries whose predecessor lies outside the block stay -1
-    // here and are stored directly by that predecessor's thread
     __shared__ __align__(16) int32_t s_nx[3 * RL_THREADS];
     __shared__ __align__(16) int32_t s_pv[3 * RL_THREADS];
+    __shared__ int4 s_task[RL_THREADS / 32][96];
     const int32_t t0 = blockIdx.x * RL_THREADS;
     const int32_t nT = min(RL_THREADS, m.T - t0);
-    const int32_t eb = 3 * t0;  // 3072-byte aligned
+    const int32_t eb = 3 * t0;
     const int32_t nE = 3 * nT;
+    const int32_t HI = 3 * m.T;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < nE; i += RL_THREADS) s_pv[i] = -1;
     __syncthreads();
     const int32_t t = t0 + threadIdx.x;
-    uint32_t fl = 0;  // the triangle's flags byte, completed after the block's links are known
-    if (threadIdx.x < nT) {
-        const int32_t HI = 3 * m.T;
-        const int32_t e0 = 3 * t;
-        int32_t tw[3], ttri[3];
-        uint32_t tloc[3], lnb[3];
+    const bool live = threadIdx.x < nT;
+    const int32_t e0 = 3 * t;
+    const int32_t lb = 3 * (int32_t)threadIdx.x;
+    uint32_t fl = 0, pend = 0;
+    int32_t tw[3], ttri[3];
+    uint32_t tloc[3], lnb[3];
+    if (live) {
         tw[0] = __ldg(m.twin + e0);
         tw[1] = __ldg(m.twin + e0 + 1);
         tw[2] = __ldg(m.twin + e0 + 2);
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w)
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const bool b = tw[k] >= HI;
-            ttri[k] = div3(tw[k]);
+            ttri[k] = b ? 0 : div3(tw[k]);
             tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
             lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
             const bool tl = !b && lnb[k] == tloc[k];
@@ -312,63 +320,83 @@ __global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w)
         const int32_t twl = lt == 0u ? tw[0] : (lt == 1u ? tw[1] : tw[2]);
         const bool seed = (twl >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < twl);
         fl = F | ((uint32_t)seed << 6);
-        const int32_t lb = 3 * (int32_t)threadIdx.x;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const int32_t e = e0 + k;
             const int j = k == 2 ? 0 : k + 1;
             if (!((F >> k) & 1u)) {
                 s_nx[lb + k] = e0 + j;
                 s_pv[lb + k] = e0 + (k == 0 ? 2 : k - 1);
-                continue;
-            }
-            int32_t x = e0 + j;
-            if (!((F >> j) & 1u)) {
-                // cross the non-frontier edge x into the neighbouring triangle
-                int32_t ty = ttri[j];      // twin of x, interior: non-frontier is not border
-                uint32_t ly = tloc[j];
-                uint32_t ley = lnb[j];     // le of tri(y)
-                int32_t steps = 0;
-                while (true) {
-                    const uint32_t lx = ly == 2u ? 0u : ly + 1u;
-                    x = 3 * ty + (int32_t)lx;               // next(y), in tri(y)
-                    const int32_t tx = __ldg(m.twin + x);
-                    if (tx >= HI) break;                     // border edge: frontier
-                    const int32_t ttx = div3(tx);
-                    const uint32_t ltx = (uint32_t)(tx - 3 * ttx);
-                    const uint32_t lex = w.le[ttx];
-                    if (ley != lx && lex != ltx) break;      // neither half longest: frontier
-                    ty = ttx;
-                    ly = ltx;
-                    ley = lex;
-                    if (++steps > w.max_rot) {
-                        atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
-                        break;
-                    }
-                }
-            }
-            s_nx[lb + k] = x;
-            const uint32_t dx = (uint32_t)(x - eb);
-            if (dx < (uint32_t)nE) s_pv[dx] = e;
-            else m.prev[x] = e;
-            if (x == tw[k]) {
-                const int32_t slot = atomicAdd(&w.ctrl->n_tips, 1);
-                if (slot < w.tip_cap) w.tips[slot] = tw[k];
-                else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+            } else if ((F >> j) & 1u) {
+                s_nx[lb + k] = e0 + j;   // successor in the same triangle
+                s_pv[lb + j] = e0 + k;
+            } else {
+                pend |= 1u << k;
             }
         }
     }
-    __syncthreads();
-    // Walk-start marks: a frontier half-edge can be its polygon's minimum
-    // only if next[e] > e and prev[e] > e.  prev[e] is known here when its
-    // predecessor lies in this block; otherwise (about 7% of frontier
-    // half-edges on the workloads measured) the mark is set whenever
-    // next[e] > e, which keeps the marks a superset of the minima.
-    if (threadIdx.x < nT) {
-        const int32_t lb = 3 * (int32_t)threadIdx.x;
+    // compact the warp's pending rotations
+    const uint32_t cnt = __popc(pend);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t slot = incl - cnt;
+    if (pend) {
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const int32_t e = 3 * t + k;
+            if ((pend >> k) & 1u) {
+                const int j = k == 2 ? 0 : k + 1;
+                s_task[wid][slot++] = make_int4(e0 + k, tw[k], ttri[j], (int32_t)(tloc[j] | (lnb[j] << 2)));
+            }
+        }
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < total; i += 32) {
+        const int4 tk = s_task[wid][i];
+        const int32_t e = tk.x;
+        int32_t ty = tk.z;
+        uint32_t ly = (uint32_t)tk.w & 3u;
+        uint32_t ley = ((uint32_t)tk.w >> 2) & 3u;
+        uint32_t lx = ly == 2u ? 0u : ly + 1u;
+        int32_t x = 3 * ty + (int32_t)lx;
+        int32_t tx = __ldg(m.twin + x);
+        int32_t steps = 0;
+        while (true) {
+            if (tx >= HI) break;                     // border edge: frontier
+            const int32_t ttx = div3(tx);
+            const uint32_t ltx = (uint32_t)(tx - 3 * ttx);
+            const uint32_t lxn = ltx == 2u ? 0u : ltx + 1u;
+            const int32_t xn = 3 * ttx + (int32_t)lxn;
+            const uint32_t lex = w.le[ttx];
+            const int32_t txn = __ldg(m.twin + xn);
+            if (ley != lx && lex != ltx) break;      // neither half longest: frontier
+            ley = lex;
+            x = xn;
+            lx = lxn;
+            tx = txn;
+            if (++steps > w.max_rot) {
+                atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
+                break;
+            }
+        }
+        s_nx[e - eb] = x;
+        const uint32_t dx = (uint32_t)(x - eb);
+        if (dx < (uint32_t)nE) s_pv[dx] = e;
+        else m.prev[x] = e;
+        if (x == tk.y) {
+            const int32_t sl = atomicAdd(&w.ctrl->n_tips, 1);
+            if (sl < w.tip_cap) w.tips[sl] = tk.y;
+            else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+        }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int32_t e = e0 + k;
             const int32_t pv = s_pv[lb + k];
             if (((fl >> k) & 1u) && s_nx[lb + k] > e && (pv < 0 || pv > e)) fl |= 8u << k;
         }

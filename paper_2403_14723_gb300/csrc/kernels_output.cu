@@ -20,8 +20,11 @@
 //                 (polygon count, length) per 2048-start chunk by per-warp
 //                 atomics
 //   k_scan_blocks exclusive scan of the chunk totals -> P, N_F
-//   k_emit        per chunk: offsets by block scan, then every minimum
-//                 writes its seed, offset and polygon (two interleaved).
+//   k_emit        per warp and 64 starts: offsets by warp scan over the
+//                 chunk prefix and the group totals before it; every
+//                 minimum writes its seed and offset and lists its polygon
+//                 (two interleaved per lane) through a per-warp shared
+//                 buffer that goes out with coalesced stores.
 #include "polylla_internal.cuh"
 
 namespace polylla {
@@ -155,8 +158,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_cand_write(MeshView m, Work w) {
 // k_walk: every start walks next until a smaller half-edge (not a minimum)
 // or back to itself (a minimum: res = polygon length).  Grid-stride, one
 // chain per lane, two chains per thread interleaved, no block barrier.  The
-// 32 starts of a warp lie in one 2048-start chunk; the warp adds their
-// (minimum count, length) into that chunk's total with one atomic.
+// 32 starts of a warp form one group, whose (minimum count, length) the warp
+// stores, and lie in one 2048-start chunk, whose total it adds with one
+// atomic.
 // ===========================================================================
 __global__ void __launch_bounds__(WALK_THREADS) k_walk(MeshView m, Work w) {
     const int32_t HI = 3 * m.T;
@@ -193,6 +197,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(MeshView m, Work w) {
         const unsigned long long s0 = warp_sum(p0);
         const unsigned long long s1 = warp_sum(p1);
         if (lane == 0) {
+            if (b0 < nc) w.grp[b0 / 32] = s0;
+            if (b0 + G < nc) w.grp[(b0 + G) / 32] = s1;
             if (s0 && b0 < nc) atomicAdd(&w.blk_b[b0 / CHUNK], s0);
             if (s1 && b0 + G < nc) atomicAdd(&w.blk_b[(b0 + G) / CHUNK], s1);
         }
@@ -200,23 +206,28 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(MeshView m, Work w) {
 }
 
 // ===========================================================================
-// k_emit: per chunk of 2048 starts (persistent grid of 1024-thread blocks):
-// thread i owns starts 2i and 2i+1 of the chunk; a block scan of their
-// (count, length) pairs plus the chunk's scanned total gives every minimum
-// its polygon index and offset.  Each minimum writes its seed and offset
-// and lists its polygon from itself along next; the two polygons of a
-// thread are listed interleaved.  Neighbouring lanes list neighbouring
-// polygons, so a warp's stores of one step fall on a few adjacent lines
-// that the next steps complete.
+// k_emit: grid-stride over groups of 64 starts, one warp each (two starts
+// per lane).  A warp scan of the (count, length) pairs, plus the chunk's
+// scanned total and the 32-start group totals of the chunk before this
+// group, gives every minimum its polygon index and offset; no block
+// barrier, so a long polygon holds up its own warp only.  Each lane lists
+// its polygons from the minimum along next, interleaved, into the warp's
+// shared buffer (entries past it go out directly); the warp then stores
+// the buffer, one contiguous range of he_list and v_list, coalesced.
 // ===========================================================================
 __global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
-    __shared__ unsigned long long s_warp[EMIT_THREADS / 32];
+    __shared__ int32_t s_he[EMIT_THREADS / 32][EMIT_BUF];
+    __shared__ int32_t s_v[EMIT_THREADS / 32][EMIT_BUF];
+    static_assert(CHUNK % 64 == 0, "groups of 64 starts do not straddle chunks");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int32_t HI = 3 * m.T;
     const int32_t nc = w.ctrl->n_cand;
-    const int32_t nchunks = w.ctrl->n_chunks;
-    static_assert(CHUNK == 2 * EMIT_THREADS, "two starts per thread");
-    for (int32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        const int32_t c0 = ch * CHUNK + 2 * threadIdx.x;
+    const int32_t n_sg = (nc + 63) / 64;
+    const int32_t nwarps = gridDim.x * (EMIT_THREADS / 32);
+    int32_t *bhe = s_he[wid];
+    int32_t *bv = s_v[wid];
+    for (int32_t sg = blockIdx.x * (EMIT_THREADS / 32) + wid; sg < n_sg; sg += nwarps) {
+        const int32_t c0 = sg * 64 + 2 * lane;
         int32_t L0 = 0, L1 = 0;
         if (c0 + 1 < nc) {
             const int2 r = *reinterpret_cast<const int2 *>(w.res + c0);  // c0 is even: 8-byte aligned
@@ -227,51 +238,75 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
         }
         const unsigned long long q0 = L0 > 0 ? ((1ull << 32) | (uint32_t)L0) : 0ull;
         const unsigned long long q1 = L1 > 0 ? ((1ull << 32) | (uint32_t)L1) : 0ull;
-        unsigned long long total;
-        const unsigned long long run = w.blk_b_pre[ch] + block_excl_scan(q0 + q1, s_warp, &total);
-        int32_t ea = -1, ka = 0, eb = -1, kb = 0;
+        const unsigned long long inc = warp_incl_scan(q0 + q1, lane);
+        const unsigned long long ex = inc - (q0 + q1);
+        const unsigned long long tot = __shfl_sync(0xffffffffu, inc, 31);
+        // groups of 32 starts [g0, gs) precede this one in its chunk (< 64)
+        const int32_t ch = (sg * 64) / CHUNK;
+        const int32_t g0 = ch * (CHUNK / 32), gs = 2 * sg;
+        unsigned long long u = 0;
+        if (g0 + lane < gs) u += w.grp[g0 + lane];
+        if (g0 + 32 + lane < gs) u += w.grp[g0 + 32 + lane];
+        const unsigned long long base = w.blk_b_pre[ch] + warp_sum(u);
+        const int32_t O0 = (int32_t)(base & 0xffffffffu);
+        const int32_t len = (int32_t)(tot & 0xffffffffu);
+        if ((int64_t)(base >> 32) + (int64_t)(tot >> 32) > (int64_t)m.T || (int64_t)O0 + len > (int64_t)HI) {
+            if (lane == 0) atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+            continue;  // warp-uniform
+        }
+        int32_t ea = -1, ka = 0, eb = -1, kb = 0;  // offsets within the group's range
         if (L0 > 0) {
-            const int32_t p = (int32_t)(run >> 32), off = (int32_t)(run & 0xffffffffu);
-            if ((int64_t)p < (int64_t)m.T && (int64_t)off + L0 <= (int64_t)HI) {
-                ea = w.cand[c0];
-                ka = off;
-                w.seeds[p] = ea;
-                w.offsets[p] = off;
-            } else {
-                atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
-            }
+            const unsigned long long r = base + ex;
+            ea = w.cand[c0];
+            ka = (int32_t)(ex & 0xffffffffu);
+            w.seeds[(int32_t)(r >> 32)] = ea;
+            w.offsets[(int32_t)(r >> 32)] = (int32_t)(r & 0xffffffffu);
         }
         if (L1 > 0) {
-            const unsigned long long r1 = run + q0;
-            const int32_t p = (int32_t)(r1 >> 32), off = (int32_t)(r1 & 0xffffffffu);
-            if ((int64_t)p < (int64_t)m.T && (int64_t)off + L1 <= (int64_t)HI) {
-                eb = w.cand[c0 + 1];
-                kb = off;
-                w.seeds[p] = eb;
-                w.offsets[p] = off;
-            } else {
-                atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
-            }
+            const unsigned long long r = base + ex + q0;
+            eb = w.cand[c0 + 1];
+            kb = (int32_t)((ex + q0) & 0xffffffffu);
+            w.seeds[(int32_t)(r >> 32)] = eb;
+            w.offsets[(int32_t)(r >> 32)] = (int32_t)(r & 0xffffffffu);
         }
         int32_t xa = ea, xb = eb, guard = 0;
         bool a = ea >= 0, b = eb >= 0;
         while (a || b) {
             if (a) {
-                w.he_list[ka] = xa;
-                w.v_list[ka] = __ldg(m.origin + xa);
+                const int32_t va = __ldg(m.origin + xa);
+                if (ka < EMIT_BUF) {
+                    bhe[ka] = xa;
+                    bv[ka] = va;
+                } else {
+                    w.he_list[O0 + ka] = xa;
+                    w.v_list[O0 + ka] = va;
+                }
                 ka++;
                 xa = m.next[xa];
                 a = xa != ea;
             }
             if (b) {
-                w.he_list[kb] = xb;
-                w.v_list[kb] = __ldg(m.origin + xb);
+                const int32_t vb = __ldg(m.origin + xb);
+                if (kb < EMIT_BUF) {
+                    bhe[kb] = xb;
+                    bv[kb] = vb;
+                } else {
+                    w.he_list[O0 + kb] = xb;
+                    w.v_list[O0 + kb] = vb;
+                }
                 kb++;
                 xb = m.next[xb];
                 b = xb != eb;
             }
             if (++guard > HI) break;
         }
+        __syncwarp();
+        const int32_t nb = min(len, EMIT_BUF);
+        for (int32_t k = lane; k < nb; k += 32) {
+            w.he_list[O0 + k] = bhe[k];
+            w.v_list[O0 + k] = bv[k];
+        }
+        __syncwarp();  // the buffer is reused by the warp's next group
     }
 }
 
@@ -292,6 +327,12 @@ __global__ void k_finish(MeshView m, Work w) {
 }
 
 int polygons_configure() { return 0; }
+
+int emit_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emit, EMIT_THREADS, 0) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
 
 void launch_cand_count(const MeshView &m, const Work &w, cudaStream_t s) {
     k_cand_count<<<w.n_cc_blocks, CC_THREADS, 0, s>>>(m, w);

@@ -104,6 +104,8 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.blk_b = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_chunk_max))) return rc;
     c->w.blk_b_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)((HI + 31) / 32)))) return rc;
+    c->w.grp = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)HI))) return rc;
     c->w.cand = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)HI))) return rc;
@@ -129,7 +131,7 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
     c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
     c->w.walk_blocks = 8 * (sms > 0 ? sms : 1);
-    c->w.emit_blocks = 2 * (sms > 0 ? sms : 1);
+    c->w.emit_blocks = emit_blocks_per_sm() * (sms > 0 ? sms : 1);
     if (polygons_configure() != 0) return cuda_fail(c, cudaGetLastError());
     c->w.max_rot = (opt && opt->max_rotation > 0) ? opt->max_rotation : 4096;
     for (int i = 0; i <= kStages; i++) {

@@ -59,6 +59,7 @@ struct Work {
     int32_t *res;                   // polygon length per start, 0 if not a minimum [3T]
     unsigned long long *blk_b;      // (minimum count, length) per CHUNK starts
     unsigned long long *blk_b_pre;  // their exclusive prefix
+    unsigned long long *grp;        // (minimum count, length) per 32 starts [ceil(3T/32)]
     int32_t n_cc_blocks;            // ceil(T / CC_TRI)
     int32_t n_chunk_max;            // ceil(3T / CHUNK)
     int32_t walk_blocks, emit_blocks;
@@ -81,7 +82,8 @@ constexpr int CC_TRI = CC_THREADS * CC_PER;
 constexpr int SCAN_THREADS = 1024;
 constexpr int CHUNK = 2048;
 constexpr int WALK_THREADS = 256;
-constexpr int EMIT_THREADS = 1024;
+constexpr int EMIT_THREADS = 512;
+constexpr int EMIT_BUF = 256;  // CSR entries staged per warp
 
 // longest-edge kernel: persistent warps, each with a two-stage ring of
 // 64-triangle tiles of origin bulk-copied (TMA) into shared memory
@@ -89,7 +91,7 @@ constexpr int LE_THREADS = 256;
 constexpr int LE_TILE = 64;
 
 // relink kernel: one thread per triangle
-constexpr int RL_THREADS = 256;
+constexpr int RL_THREADS = 128;
 
 // bounded waits: iterations of an mbarrier try_wait loop before giving up
 constexpr int MBAR_WAIT_LIMIT = 1 << 22;
@@ -165,5 +167,6 @@ void launch_walk(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);  // two kernels
 void launch_emit(const MeshView &m, const Work &w, cudaStream_t s);
 int polygons_configure();
+int emit_blocks_per_sm();
 
 }  // namespace polylla

@@ -36,7 +36,8 @@ constexpr size_t OFF_BLK_A = OFF_CHORDS + up256(4 * (size_t)NA_MAX_V);
 constexpr size_t OFF_BLK_A_PRE = OFF_BLK_A + up256(8 * (size_t)NA_MAX_CC);
 constexpr size_t OFF_BLK_B = OFF_BLK_A_PRE + up256(8 * (size_t)NA_MAX_CC);
 constexpr size_t OFF_BLK_B_PRE = OFF_BLK_B + up256(8 * (size_t)NA_MAX_CHUNKS);
-constexpr size_t OFF_CAND = OFF_BLK_B_PRE + up256(8 * (size_t)NA_MAX_CHUNKS);
+constexpr size_t OFF_GRP = OFF_BLK_B_PRE + up256(8 * (size_t)NA_MAX_CHUNKS);
+constexpr size_t OFF_CAND = OFF_GRP + up256(8 * (size_t)((NA_MAX_HI + 31) / 32));
 constexpr size_t OFF_RES = OFF_CAND + up256(4 * (size_t)NA_MAX_HI);
 constexpr size_t OFF_CTRL = OFF_RES + up256(4 * (size_t)NA_MAX_HI);
 constexpr size_t NA_BYTES = OFF_CTRL + up256(sizeof(DevCtrl));
@@ -109,6 +110,7 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.blk_a_pre = reinterpret_cast<unsigned long long *>(base + OFF_BLK_A_PRE);
     w.blk_b = reinterpret_cast<unsigned long long *>(base + OFF_BLK_B);
     w.blk_b_pre = reinterpret_cast<unsigned long long *>(base + OFF_BLK_B_PRE);
+    w.grp = reinterpret_cast<unsigned long long *>(base + OFF_GRP);
     w.cand = reinterpret_cast<int32_t *>(base + OFF_CAND);
     w.res = reinterpret_cast<int32_t *>(base + OFF_RES);
     w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
@@ -122,7 +124,7 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
     w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
     w.walk_blocks = 8 * (sms > 0 ? sms : 1);
-    w.emit_blocks = 2 * (sms > 0 ? sms : 1);
+    w.emit_blocks = emit_blocks_per_sm() * (sms > 0 ? sms : 1);
 
     // The first kernel zeroes the control block and k_cand_count zeroes the
     // chunk totals; every other scratch word is written before it is read,
