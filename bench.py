@@ -9,6 +9,13 @@ workload is the largest single mesh: the 4096 x 4096 perturbed grid
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle, timed on the host
+    python bench.py --workload batch_4096  # 4,096 meshes in one batched run
+
+The batched workload (4,096 independent triangulations, sizes log-uniform in
+[100, 200,000] triangles, alternately Delaunay and perturbed grids) runs
+every stage once over all meshes from a CUDA graph with autotuned launch
+settings, and reports beside it the plain one-mesh-at-a-time path on the
+same meshes.
 
 Under torchrun (N > 1) every rank runs its own replica of the mesh on its own
 GPU (a single mesh does not shard); value = triangles of all ranks / max
@@ -205,6 +212,8 @@ def algorithmic_bytes(T, V, NF, P):
         "walk": 4 * NF,                              # next of every frontier half-edge once
         "chunk_scan": 0,
         "emit": 4 * NF + 4 * NF + 8 * NF + 8 * P,    # next, origin; CSR out
+        "batch_pack": 0,                             # batches only
+        "batch_unpack": 0,
     }
     return total, per_stage
 
@@ -215,6 +224,13 @@ def algorithmic_bytes(T, V, NF, P):
 
 def ref_sample_mesh(workload: str):
     from paper_2403_14723_gb300 import meshgen
+
+    if workload.startswith("batch_"):
+        # the first 64 meshes of the batch recipe; the oracle runs them one by one
+        r = BATCH_RECIPE
+        sizes = meshgen.batch_sizes(int(workload.split("_")[1]), r["t_min"], r["t_max"], r["seed"])[:64]
+        ms = [meshgen.batch_member(i, int(t), r["seed"]) for i, t in enumerate(sizes)]
+        return ms, f"the first {len(ms)} meshes of the batch ({sum(m.n_triangles for m in ms):,} triangles)"
 
     if workload.startswith("pgrid_"):
         return meshgen.perturbed_grid(2048, 0.3, seed=3), "perturbed grid 2048x2048 (8,380,418 triangles), same recipe"
@@ -230,23 +246,26 @@ def run_reference(args):
     import oracle
 
     mesh, sample = ref_sample_mesh(args.workload)
+    meshes = mesh if isinstance(mesh, list) else [mesh]
+    n_tri = sum(m.n_triangles for m in meshes)
     oracle.build()
     times = []
+    n_poly = 0
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.run_mesh(mesh)
+        n_poly = sum(oracle.run_mesh(m).n_polygons for m in meshes)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
     tot = sum(times)
-    value = mesh.n_triangles * len(times) / tot
+    value = n_tri * len(times) / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample, "triangles": mesh.n_triangles,
-                   "polygons": r.n_polygons},
+        "config": {"workload": args.workload, "sample": sample, "triangles": n_tri,
+                   "polygons": n_poly},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{sample}; single-threaded sequential oracle, {len(times)} timed runs"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -400,10 +419,203 @@ def run_gb300(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched workload: many meshes, one launch per stage
+# ---------------------------------------------------------------------------
+
+BATCH_RECIPE = {"meshes": 4096, "t_min": 100, "t_max": 200_000, "seed": 4}
+
+
+def batch_meshes(n_meshes: int):
+    from paper_2403_14723_gb300 import meshgen
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    r = BATCH_RECIPE
+    return meshgen.random_batch(n_meshes, r["t_min"], r["t_max"], r["seed"], workers=workers)
+
+
+def run_batched(args):
+    n_meshes = int(args.workload.split("_")[1])
+    meshes = batch_meshes(n_meshes)        # process pool, before any CUDA call
+    import numpy as np
+    import torch
+
+    from paper_2403_14723_gb300 import build, polylla
+
+    rank, ws, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build_library()
+    db = polylla.DeviceBatch.from_host(meshes, device=dev)
+    T = int(db.triangle_offset[-1])
+    V = int(db.vertex_offset[-1])
+    H = int(db.halfedge_offset[-1])
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    with torch.cuda.stream(stream):
+        ctx = polylla.polylla_batch_create(db, stream=stream)
+        tuning = polylla.polylla_autotune(ctx, reps=3, stream=stream)
+
+        # per-stage times (CUDA events on the launching stream), untimed region
+        polylla.polylla_set_timing(ctx, True)
+        stage_acc = {}
+        for i in range(10):
+            flush.fill_(i)
+            polylla.polylla_generate(ctx, stream)
+            for k, v in polylla.polylla_get_stage_times(ctx).items():
+                stage_acc.setdefault(k, []).append(v)
+        polylla.polylla_set_timing(ctx, False)
+        stage_ms = {k: statistics.mean(v) for k, v in stage_acc.items()}
+
+        # without a graph (stream launches), a few steps
+        def timed(k, fn):
+            st = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            en = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            for i in range(k):
+                flush.fill_(i)
+                st[i].record(stream)
+                fn()
+                en[i].record(stream)
+            stream.synchronize()
+            return statistics.mean(s.elapsed_time(e) for s, e in zip(st, en))
+
+        def step():
+            polylla.polylla_generate(ctx, stream)
+
+        for _ in range(3):
+            step()
+        ms_nograph = timed(max(3, min(args.steps, 20)), step)
+        polylla.polylla_capture_graph(ctx, stream)
+        for _ in range(max(args.warmup, 3)):
+            step()
+        stream.synchronize()
+        dist_barrier(ws)
+        with ClockSampler(local) as clk:
+            ms = timed(args.steps, step)
+        dist_barrier(ws)
+        ms = dist_max(ms, ws)
+        launches = args.steps * 15
+        out = polylla.polylla_get_polygons(ctx, stream)
+        P, NF = out["n_polygons"], out["n_frontier"]
+        po = polylla.polylla_batch_polygon_offsets(ctx, n_meshes).cpu().numpy()
+
+        # ---- the plain one-mesh-at-a-time path on the same meshes --------
+        dms = [polylla.DeviceMesh.from_host(m, device=dev) for m in meshes]
+        ctxs = [polylla.polylla_create(d, stream=stream) for d in dms]
+
+        def loop():
+            for c in ctxs:
+                polylla.polylla_generate(c, stream)
+
+        loop()
+        ms_loop = dist_max(timed(3, loop), ws)
+        p_loop = [polylla.polylla_get_polygons(c, stream)["n_polygons"] for c in ctxs]
+        assert np.array_equal(np.diff(po), np.array(p_loop)), "batched and per-mesh polygon counts differ"
+        for c in ctxs:
+            polylla.polylla_destroy(c)
+        del dms
+
+        # ---- end to end: host arrays in, CSR and links out, copies timed ---
+        e2e = None
+        if not args.no_e2e:
+            host = {k: torch.from_numpy(np.concatenate([getattr(m, k) for m in meshes])).pin_memory()
+                    for k in ("coords", "origin", "twin", "next", "prev")}
+            o_he = torch.empty(NF, dtype=torch.int32).pin_memory()
+            o_v = torch.empty(NF, dtype=torch.int32).pin_memory()
+            o_seed = torch.empty(P, dtype=torch.int32).pin_memory()
+            o_off = torch.empty(P + 1, dtype=torch.int32).pin_memory()
+            o_po = torch.empty(n_meshes + 1, dtype=torch.int32).pin_memory()
+            o_nx = torch.empty(H, dtype=torch.int32).pin_memory()
+            o_pv = torch.empty(H, dtype=torch.int32).pin_memory()
+
+            def e2e_step():
+                for k in ("coords", "origin", "twin", "next", "prev"):
+                    getattr(db, k).copy_(host[k], non_blocking=True)
+                polylla.polylla_generate(ctx, stream)
+                o = polylla.polylla_get_polygons(ctx, stream)
+                o_he.copy_(o["he_list"], non_blocking=True)
+                o_v.copy_(o["v_list"], non_blocking=True)
+                o_seed.copy_(o["seeds"], non_blocking=True)
+                o_off.copy_(o["offsets"], non_blocking=True)
+                o_po.copy_(polylla.polylla_batch_polygon_offsets(ctx, n_meshes), non_blocking=True)
+                o_nx.copy_(db.next, non_blocking=True)
+                o_pv.copy_(db.prev, non_blocking=True)
+                stream.synchronize()
+
+            e2e_step()
+            e_steps = max(3, min(args.steps, 10))
+            dist_barrier(ws)
+            t0 = time.perf_counter()
+            for _ in range(e_steps):
+                e2e_step()
+            e_ms = dist_max(1e3 * (time.perf_counter() - t0) / e_steps, ws)
+            h2d = 16 * V + 4 * 4 * H
+            d2h = 4 * (2 * NF + P + (P + 1) + (n_meshes + 1) + 2 * H) + 32
+            e2e = {"value": ws * T / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "api": "pinned host arrays -> polylla_generate (batch, CUDA graph) -> CSR and links back"}
+        polylla.polylla_destroy(ctx)
+
+    total_alg, per_stage = algorithmic_bytes(T, V, NF, P)
+    per_stage["batch_pack"] = 16 * H                 # local origin/twin in, union out
+    per_stage["batch_unpack"] = 48 * T               # union next/prev in, local out
+    dominant = max(stage_ms, key=stage_ms.get)
+    peak, peak_kind = measured_peaks()
+    ach = per_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": ncu_traffic(dominant),
+                "algorithmic_bytes": per_stage[dominant], "stage_ms": stage_ms,
+                "whole_step": {"algorithmic_bytes": total_alg, "achieved": total_alg / (ms * 1e-3) / 1e9,
+                               "frac": total_alg / (ms * 1e-3) / 1e9 / peak}}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        sample = meshes[: min(len(meshes), 256)]
+        t0 = time.perf_counter()
+        for m in sample:
+            oracle.run_mesh(m)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sum(m.n_triangles for m in sample) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {len(sample)} meshes of the batch "
+                         f"({sum(m.n_triangles for m in sample):,} triangles), one pass, single-threaded"}
+    clocks = clk.summary()
+    if rank == 0:
+        r = BATCH_RECIPE
+        line = {
+            "metric": METRIC, "value": ws * T / (ms * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/int32", "data": "synthetic",
+            "config": {"workload": args.workload, "meshes": n_meshes, "triangles": T, "vertices": V,
+                       "halfedges": H, "polygons": P, "frontier_halfedges": NF,
+                       "sizes": f"log-uniform [{r['t_min']}, {r['t_max']}] triangles, seed {r['seed']}; "
+                                "even meshes Delaunay of uniform points, odd perturbed grids (jitter 0.3)",
+                       "parallelism": f"replicas x{ws}", "cuda_graph": True, "tuning": tuning,
+                       "l2": "256 MiB buffer written between timed steps; inputs exceed L2"},
+            "one_mesh_at_a_time": {"value": ws * T / (ms_loop * 1e-3), "unit": UNIT, "ms_per_step": ms_loop,
+                                   "launches_per_step": 11 * n_meshes,
+                                   "how": "polylla_generate per mesh, back to back on one stream"},
+            "without_graph": {"value": ws * T / (ms_nograph * 1e-3), "unit": UNIT, "ms_per_step": ms_nograph},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "kernel_digest": kernel_digest(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batch_"):
+        return run_batched(args)
     return run_gb300(args)
 
 

@@ -198,19 +198,99 @@ int polylla_generate_host(polylla_ctx *ctx, const polylla_host_mesh *in,
                           polylla_host_result *out, int32_t validate, polylla_stream stream);
 
 /*
- * Per-stage timing.  With timing enabled, generate records a CUDA event
- * around each kernel it launches (on the generate stream);
+ * Per-stage timing.  With timing enabled, generate records a pair of CUDA
+ * events around each stage it runs (on the generate stream);
  * polylla_get_stage_times synchronizes and writes the milliseconds of up to
- * n stages of the last generate, returning how many it wrote.
- * polylla_stage_name gives the kernel name of stage i.
+ * n stages of the last generate (0 for a stage that did not run: the two
+ * batch stages on a single mesh), returning how many it wrote, or 0 when
+ * the last generate was not timed (timing off, or a captured graph).
+ * polylla_stage_name gives the name of stage i: the ten stages of the
+ * method, then "batch_pack" and "batch_unpack".
  * polylla_launch_count gives the number of kernels the last generate
- * launched.
+ * launched (11 for a mesh, 15 for a batch).
  */
 int polylla_set_timing(polylla_ctx *ctx, int32_t enable);
 int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
 int polylla_stage_count(void);
 const char *polylla_stage_name(int32_t i);
 int polylla_launch_count(polylla_ctx *ctx);
+
+/*
+ * Batches (no counterpart in the paper, whose method takes one mesh).
+ *
+ * n independent triangulations, each in the single-mesh layout above with
+ * its own local indices (vertex ids from 0, interior half-edges [0, 3T_i),
+ * border half-edges [3T_i, H_i)), concatenated: mesh i's vertices are rows
+ * [vertex_offset[i], vertex_offset[i+1]) of coords and its half-edges
+ * entries [halfedge_offset[i], halfedge_offset[i+1]) of origin/twin/next/
+ * prev.  The offset arrays are HOST prefix sums with n+1 entries starting
+ * at 0 (copied at create); every mesh has V_i >= 3, T_i >= 1,
+ * H_i >= 3 T_i + 3; the totals obey the single-mesh limits.
+ *
+ * polylla_batch_create validates every mesh (as polylla_create, plus range
+ * checks of each local index) and allocates for the whole batch: scratch
+ * as for one mesh of the total size plus 16 bytes per half-edge for the
+ * batch's union.  The device arrays are not copied and must stay valid.
+ * polylla_generate on a batch context runs the method once over all meshes
+ * -- one launch per stage, not one per mesh -- and gives each mesh exactly
+ * what polylla_generate gives it alone: next/prev of its interior half-
+ * edges are rewritten in its local indices; polylla_get_polygons returns
+ * one CSR for the batch, ordered by mesh and then by seed, with seeds,
+ * he_list and v_list in each mesh's local indices and offsets into the
+ * batch's he_list.  polylla_batch_polygon_offsets hands out a device array
+ * of n+1 entries, valid after a generate completes: mesh i owns polygons
+ * [poly_offset[i], poly_offset[i+1]).  polylla_get_labels reports the
+ * union's labels (triangles in batch order).  polylla_generate_host does
+ * not take a batch context.
+ */
+typedef struct {
+    int32_t n_meshes;
+    const int32_t *vertex_offset;   /* HOST [n+1] */
+    const int32_t *triangle_offset; /* HOST [n+1] */
+    const int32_t *halfedge_offset; /* HOST [n+1] */
+    const double *coords;           /* DEVICE [V_total][2], 16-byte aligned */
+    const int32_t *origin, *twin;   /* DEVICE [H_total], local indices */
+    int32_t *next, *prev;           /* DEVICE [H_total], local; interior entries rewritten */
+} polylla_batch;
+int polylla_batch_create(polylla_ctx **out, const polylla_batch *batch,
+                         const polylla_options *opt, polylla_stream stream);
+int polylla_batch_polygon_offsets(polylla_ctx *ctx, const int32_t **poly_offset);
+
+/*
+ * CUDA graphs.  polylla_capture_graph records one whole generate of the
+ * context (its kernels, with the current launch settings) into a CUDA graph
+ * on stream (which must not be NULL, the legacy stream cannot be captured);
+ * from then on polylla_generate launches that graph, one launch instead of
+ * 11 or 15, untimed.  Changing the launch settings (polylla_set_tuning,
+ * polylla_autotune) or polylla_release_graph drops the graph.  The graph
+ * reads and writes the same device arrays as the captured generate.
+ */
+int polylla_capture_graph(polylla_ctx *ctx, polylla_stream stream);
+int polylla_release_graph(polylla_ctx *ctx);
+
+/*
+ * Launch tuning (results never depend on it).  relink_threads is the block
+ * size of the relink kernel (64, 128 or 256); the others are the grid sizes
+ * (blocks) of the persistent longest-edge, walk and emit kernels, each in
+ * [1, 64 * SMs].  polylla_autotune times whole generates (reps per setting,
+ * median of the stage's CUDA-event time), tries the candidates of one
+ * setting at a time in stage order and keeps the fastest, applies the
+ * result to the context, stores it in a process-wide table per device and
+ * size bucket (floor(log2 T), T the mesh's or batch's triangle count) that
+ * contexts created later start from, and writes it to *out (may be NULL).
+ * It runs generate on the context's mesh (idempotent) and synchronizes
+ * stream.  polylla_tuning_cache_clear empties the table.
+ */
+typedef struct {
+    int32_t relink_threads;
+    int32_t longest_edge_blocks;
+    int32_t walk_blocks;
+    int32_t emit_blocks;
+} polylla_tuning;
+int polylla_get_tuning(polylla_ctx *ctx, polylla_tuning *out);
+int polylla_set_tuning(polylla_ctx *ctx, const polylla_tuning *tuning);
+int polylla_autotune(polylla_ctx *ctx, int32_t reps, polylla_tuning *out, polylla_stream stream);
+int polylla_tuning_cache_clear(void);
 
 /*
  * polylla_generate_noalloc -- the whole method, allocating nothing.

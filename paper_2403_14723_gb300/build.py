@@ -17,7 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["polylla_api.cu", "kernels_label.cu", "kernels_repair.cu", "kernels_output.cu",
+SOURCES = ["polylla_api.cu", "kernels_label.cu", "kernels_repair.cu", "kernels_output.cu", "kernels_batch.cu",
            "polylla_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "polylla_internal.cuh"), os.path.join(INCLUDE, "polylla.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,252 @@
+// Batches of independent meshes (no counterpart in the paper, whose method
+// takes one mesh): the stage kernels run once over the batch's union, a
+// single mesh whose connected components are the batch's meshes.  Packing
+// renumbers each mesh's local indices into the union; unpacking writes the
+// relinked next/prev back in local indices and finds each mesh's polygons.
+//
+// The union keeps every order the method depends on within a mesh: interior
+// half-edges of mesh i are shifted by 3 t_off[i], its border half-edges go
+// after all interior ones (still after its own interior ones, still in
+// order), so longest-edge ties (smallest edge id), rotation, canonical seeds
+// (smallest half-edge) and the polygon order (by seed) are those of the
+// mesh alone, and mesh i's polygons come before mesh i+1's.
+#include "polylla_internal.cuh"
+
+namespace polylla {
+
+constexpr int BP_THREADS = 256;
+constexpr int BP_ITEMS = 8;
+constexpr int BP_SPAN = BP_THREADS * BP_ITEMS;
+constexpr int BP_TABLE = 48;  // meshes a block keeps in shared memory
+
+// Per-mesh constants of the meshes a block's range touches, in shared
+// memory: for interior blocks the range [base, end) of union half-edges
+// starts in mesh m0.  Entry j describes mesh m0 + j: the union index its
+// segment starts at (interior: 3 t_off, border: 3T_tot + b_off), the
+// offset from union to concatenated local position, the vertex offset, and
+// the border shift (union index of local border half-edge y is bo + y).
+struct PackTable {
+    int32_t m0, n;
+    int32_t start[BP_TABLE + 1];
+    int32_t to_local[BP_TABLE];   // g = x + to_local
+    int32_t t3[BP_TABLE];         // 3 t_off: interior shift
+    int32_t ti3[BP_TABLE];        // 3 T_i
+    int32_t bo[BP_TABLE];
+    int32_t v0[BP_TABLE];
+    int32_t hi[BP_TABLE];         // H_i
+    int32_t vi[BP_TABLE];         // V_i
+};
+
+// fill the table (block-wide); returns false when the range spans more
+// meshes than the table holds (then every element looks its mesh up)
+__device__ bool pack_table(const BatchView &b, bool border, int32_t base, int32_t end, PackTable &tb) {
+    const int32_t HI = 3 * b.T_tot;
+    if (threadIdx.x == 0) {
+        int32_t m0, m1;
+        if (!border) {
+            m0 = seg_of(b.t_off, b.n, base / 3);
+            m1 = seg_of(b.t_off, b.n, (end - 1) / 3);
+        } else {
+            m0 = seg_of(b.b_off, b.n, base - HI);
+            m1 = seg_of(b.b_off, b.n, end - 1 - HI);
+        }
+        tb.m0 = m0;
+        tb.n = m1 - m0 + 1;
+    }
+    __syncthreads();
+    const int32_t n = tb.n;
+    if (n > BP_TABLE) return false;
+    for (int j = threadIdx.x; j < n; j += BP_THREADS) {
+        const int32_t m = tb.m0 + j;
+        const int32_t t0 = b.t_off[m], Ti = b.t_off[m + 1] - t0;
+        const int32_t h0 = b.h_off[m], bb = b.b_off[m];
+        tb.t3[j] = 3 * t0;
+        tb.ti3[j] = 3 * Ti;
+        tb.bo[j] = HI + bb - 3 * Ti;
+        tb.v0[j] = b.v_off[m];
+        tb.hi[j] = b.h_off[m + 1] - h0;
+        tb.vi[j] = b.v_off[m + 1] - b.v_off[m];
+        if (!border) {
+            tb.start[j] = 3 * t0;
+            tb.to_local[j] = h0 - 3 * t0;              // g = h0 + (x - 3 t0)
+        } else {
+            tb.start[j] = HI + bb;
+            tb.to_local[j] = h0 + 3 * Ti - HI - bb;    // g = h0 + 3 Ti + (x - HI - bb)
+        }
+    }
+    if (threadIdx.x == 0) tb.start[n] = 0x7fffffff;
+    __syncthreads();
+    return true;
+}
+
+// ===========================================================================
+// k_batch_pack: union origin/twin (and next/prev when given) from the local
+// arrays.  Blocks [0, nbI) cover interior union half-edges, the rest the
+// border ones; a block tabulates the meshes its range touches and each
+// element finds its mesh there.  With bad != nullptr every local value is
+// range-checked (create).
+// ===========================================================================
+__global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t *u_origin, int32_t *u_twin,
+                                                           int32_t *u_next, int32_t *u_prev, int32_t *bad) {
+    __shared__ PackTable tb;
+    const int32_t HI = 3 * b.T_tot;
+    const int32_t nbI = (HI + BP_SPAN - 1) / BP_SPAN;
+    const bool border = (int32_t)blockIdx.x >= nbI;
+    const int32_t base = border ? HI + ((int32_t)blockIdx.x - nbI) * BP_SPAN : (int32_t)blockIdx.x * BP_SPAN;
+    const int32_t end = min(base + BP_SPAN, border ? b.H_tot : HI);
+    const bool tabled = pack_table(b, border, base, end, tb);
+    // all loads of the thread's items first, then all stores: the stores
+    // could alias later loads as far as the compiler knows, which would
+    // otherwise serialise one memory round trip per item
+    int32_t o[BP_ITEMS], tw[BP_ITEMS], nx[BP_ITEMS], pv[BP_ITEMS], jj[BP_ITEMS];
+    int32_t j = 0;
+#pragma unroll
+    for (int k = 0; k < BP_ITEMS; k++) {
+        const int32_t x = base + k * BP_THREADS + (int32_t)threadIdx.x;
+        jj[k] = -1;
+        if (x >= end) continue;
+        int32_t g;
+        if (tabled) {
+            while (tb.start[j + 1] <= x) j++;
+            g = x + tb.to_local[j];
+            jj[k] = j;
+        } else {
+            const int32_t m = border ? seg_of(b.b_off, b.n, x - HI) : seg_of(b.t_off, b.n, x / 3);
+            const int32_t t0 = b.t_off[m], Ti = b.t_off[m + 1] - t0;
+            g = border ? b.h_off[m] + 3 * Ti + (x - HI - b.b_off[m]) : b.h_off[m] + (x - 3 * t0);
+            jj[k] = m;
+        }
+        o[k] = b.origin[g];
+        tw[k] = b.twin[g];
+        if (u_next) {
+            nx[k] = b.next[g];
+            pv[k] = b.prev[g];
+        }
+    }
+    int32_t fail = 0;
+#pragma unroll
+    for (int k = 0; k < BP_ITEMS; k++) {
+        if (jj[k] < 0) continue;
+        const int32_t x = base + k * BP_THREADS + (int32_t)threadIdx.x;
+        int32_t t3, ti3, bo, v0, hi, vi;
+        if (tabled) {
+            const int32_t q = jj[k];
+            t3 = tb.t3[q];
+            ti3 = tb.ti3[q];
+            bo = tb.bo[q];
+            v0 = tb.v0[q];
+            hi = tb.hi[q];
+            vi = tb.vi[q];
+        } else {
+            const int32_t m = jj[k];
+            const int32_t t0 = b.t_off[m], Ti = b.t_off[m + 1] - t0;
+            t3 = 3 * t0;
+            ti3 = 3 * Ti;
+            bo = HI + b.b_off[m] - 3 * Ti;
+            v0 = b.v_off[m];
+            hi = b.h_off[m + 1] - b.h_off[m];
+            vi = b.v_off[m + 1] - v0;
+        }
+        if (bad) fail |= o[k] < 0 || o[k] >= vi || tw[k] < 0 || tw[k] >= hi;
+        u_origin[x] = o[k] + v0;
+        u_twin[x] = tw[k] < ti3 ? t3 + tw[k] : bo + tw[k];
+        if (u_next) {
+            if (bad) fail |= nx[k] < 0 || nx[k] >= hi || pv[k] < 0 || pv[k] >= hi;
+            u_next[x] = nx[k] < ti3 ? t3 + nx[k] : bo + nx[k];
+            u_prev[x] = pv[k] < ti3 ? t3 + pv[k] : bo + pv[k];
+        }
+    }
+    if (fail) atomicOr(bad, 1);
+}
+
+// ===========================================================================
+// k_batch_unpack: relinked next/prev of every interior union half-edge back
+// into the mesh's local arrays (a relinked successor or predecessor of an
+// interior half-edge is an interior half-edge of the same mesh).  Loads of
+// all items first, then the stores, as in the pack.
+// ===========================================================================
+__global__ void __launch_bounds__(BP_THREADS) k_batch_unpack(BatchView b, const int32_t *u_next,
+                                                             const int32_t *u_prev) {
+    __shared__ PackTable tb;
+    const int32_t HI = 3 * b.T_tot;
+    const int32_t base = (int32_t)blockIdx.x * BP_SPAN;
+    const int32_t end = min(base + BP_SPAN, HI);
+    const bool tabled = pack_table(b, false, base, end, tb);
+    int32_t nx[BP_ITEMS], pv[BP_ITEMS];
+#pragma unroll
+    for (int k = 0; k < BP_ITEMS; k++) {
+        const int32_t x = base + k * BP_THREADS + (int32_t)threadIdx.x;
+        if (x < end) {
+            nx[k] = u_next[x];
+            pv[k] = u_prev[x];
+        }
+    }
+    int32_t j = 0;
+#pragma unroll
+    for (int k = 0; k < BP_ITEMS; k++) {
+        const int32_t x = base + k * BP_THREADS + (int32_t)threadIdx.x;
+        if (x >= end) break;
+        int32_t shift, g;
+        if (tabled) {
+            while (tb.start[j + 1] <= x) j++;
+            shift = tb.t3[j];
+            g = x + tb.to_local[j];
+        } else {
+            const int32_t m = seg_of(b.t_off, b.n, x / 3);
+            shift = 3 * b.t_off[m];
+            g = b.h_off[m] + (x - shift);
+        }
+        b.next[g] = nx[k] - shift;
+        b.prev[g] = pv[k] - shift;
+    }
+}
+
+// ===========================================================================
+// k_batch_ranges: poly_off[i] = number of polygons whose (union) seed lies
+// below mesh i's first half-edge, i.e. mesh i owns polygons
+// [poly_off[i], poly_off[i+1]); poly_off[n] = P.
+// k_batch_seeds: then each seed becomes local; a polygon's list starts at its
+// seed and the emitted lists are already local, so seed = he_list[offsets[p]].
+// ===========================================================================
+__global__ void k_batch_ranges(BatchView b, const int32_t *seeds, const DevCtrl *ctrl, int32_t *poly_off) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > b.n) return;
+    const int32_t P = ctrl->n_polygons;
+    if (i == b.n) {
+        poly_off[i] = P;
+        return;
+    }
+    const int32_t key = 3 * b.t_off[i];
+    int32_t lo = 0, hi = P;  // first p with seeds[p] >= key
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (seeds[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    poly_off[i] = lo;
+}
+
+__global__ void k_batch_seeds(int32_t *seeds, const int32_t *offsets, const int32_t *he_list, const DevCtrl *ctrl) {
+    const int32_t P = ctrl->n_polygons;
+    for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+        seeds[p] = he_list[offsets[p]];
+}
+
+void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
+                       int32_t *bad, cudaStream_t s) {
+    const int32_t HI = 3 * b.T_tot, HB = b.H_tot - HI;
+    const int32_t blocks = (HI + BP_SPAN - 1) / BP_SPAN + (HB + BP_SPAN - 1) / BP_SPAN;
+    k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad);
+}
+
+void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s) {
+    const int32_t blocks = (3 * b.T_tot + BP_SPAN - 1) / BP_SPAN;
+    k_batch_unpack<<<blocks, BP_THREADS, 0, s>>>(b, u.next, u.prev);
+}
+
+void launch_batch_ranges(const BatchView &b, const Work &w, int32_t *poly_off, cudaStream_t s) {
+    k_batch_ranges<<<(b.n + 1 + 255) / 256, 256, 0, s>>>(b, w.seeds, w.ctrl, poly_off);
+    k_batch_seeds<<<w.persistent_blocks, 256, 0, s>>>(w.seeds, w.offsets, w.he_list, w.ctrl);
+}
+
+}  // namespace polylla

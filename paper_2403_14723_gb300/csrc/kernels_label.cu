@@ -282,17 +282,18 @@ __device__ __forceinline__ int32_t div3(int32_t x) { return (int32_t)((uint32_t)
 // same triangle; the others (the successor lies across a non-frontier edge)
 // become tasks that the warp's lanes then take one each, so a warp runs its
 // rotations side by side instead of once per local half-edge.
-__global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w) {
-    __shared__ __align__(16) int32_t s_nx[3 * RL_THREADS];
-    __shared__ __align__(16) int32_t s_pv[3 * RL_THREADS];
-    __shared__ int4 s_task[RL_THREADS / 32][96];
-    const int32_t t0 = blockIdx.x * RL_THREADS;
-    const int32_t nT = min(RL_THREADS, m.T - t0);
+template <int NT>
+__global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
+    __shared__ __align__(16) int32_t s_nx[3 * NT];
+    __shared__ __align__(16) int32_t s_pv[3 * NT];
+    __shared__ int4 s_task[NT / 32][96];
+    const int32_t t0 = blockIdx.x * NT;
+    const int32_t nT = min(NT, m.T - t0);
     const int32_t eb = 3 * t0;
     const int32_t nE = 3 * nT;
     const int32_t HI = 3 * m.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < nE; i += RL_THREADS) s_pv[i] = -1;
+    for (int i = threadIdx.x; i < nE; i += NT) s_pv[i] = -1;
     __syncthreads();
     const int32_t t = t0 + threadIdx.x;
     const bool live = threadIdx.x < nT;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w)
         w.flags[t] = (uint8_t)fl;
     }
     int4 *dn = reinterpret_cast<int4 *>(m.next + eb);
-    for (int i = threadIdx.x; 4 * i < nE; i += RL_THREADS) {
+    for (int i = threadIdx.x; 4 * i < nE; i += NT) {
         if (4 * i + 3 < nE) {
             dn[i] = reinterpret_cast<const int4 *>(s_nx)[i];
         } else {
@@ -411,15 +412,18 @@ __global__ void __launch_bounds__(RL_THREADS) k_label_relink(MeshView m, Work w)
                 if (4 * i + q < nE) m.next[eb + 4 * i + q] = s_nx[4 * i + q];
         }
     }
-    for (int i = threadIdx.x; i < nE; i += RL_THREADS) {
+    for (int i = threadIdx.x; i < nE; i += NT) {
         const int32_t v = s_pv[i];
         if (v >= 0) m.prev[eb + i] = v;
     }
 }
 
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
-    int blocks = (m.T + RL_THREADS - 1) / RL_THREADS;
-    k_label_relink<<<blocks, RL_THREADS, 0, s>>>(m, w);
+    switch (w.rl_threads) {
+        case 64: k_label_relink<64><<<(m.T + 63) / 64, 64, 0, s>>>(m, w); break;
+        case 256: k_label_relink<256><<<(m.T + 255) / 256, 256, 0, s>>>(m, w); break;
+        default: k_label_relink<128><<<(m.T + 127) / 128, 128, 0, s>>>(m, w); break;
+    }
 }
 
 }  // namespace polylla

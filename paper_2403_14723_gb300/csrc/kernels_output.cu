@@ -269,16 +269,30 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
             w.seeds[(int32_t)(r >> 32)] = eb;
             w.offsets[(int32_t)(r >> 32)] = (int32_t)(r & 0xffffffffu);
         }
+        // in a batch, lists are written in the mesh's own indices
+        int32_t she_a = 0, sv_a = 0, she_b = 0, sv_b = 0;
+        if (w.loc_n > 0) {
+            if (ea >= 0) {
+                const int32_t i = seg_of(w.loc_t_off, w.loc_n, ea / 3);
+                she_a = 3 * __ldg(w.loc_t_off + i);
+                sv_a = __ldg(w.loc_v_off + i);
+            }
+            if (eb >= 0) {
+                const int32_t i = seg_of(w.loc_t_off, w.loc_n, eb / 3);
+                she_b = 3 * __ldg(w.loc_t_off + i);
+                sv_b = __ldg(w.loc_v_off + i);
+            }
+        }
         int32_t xa = ea, xb = eb, guard = 0;
         bool a = ea >= 0, b = eb >= 0;
         while (a || b) {
             if (a) {
-                const int32_t va = __ldg(m.origin + xa);
+                const int32_t va = __ldg(m.origin + xa) - sv_a;
                 if (ka < EMIT_BUF) {
-                    bhe[ka] = xa;
+                    bhe[ka] = xa - she_a;
                     bv[ka] = va;
                 } else {
-                    w.he_list[O0 + ka] = xa;
+                    w.he_list[O0 + ka] = xa - she_a;
                     w.v_list[O0 + ka] = va;
                 }
                 ka++;
@@ -286,12 +300,12 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
                 a = xa != ea;
             }
             if (b) {
-                const int32_t vb = __ldg(m.origin + xb);
+                const int32_t vb = __ldg(m.origin + xb) - sv_b;
                 if (kb < EMIT_BUF) {
-                    bhe[kb] = xb;
+                    bhe[kb] = xb - she_b;
                     bv[kb] = vb;
                 } else {
-                    w.he_list[O0 + kb] = xb;
+                    w.he_list[O0 + kb] = xb - she_b;
                     w.v_list[O0 + kb] = vb;
                 }
                 kb++;

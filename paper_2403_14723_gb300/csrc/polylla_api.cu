@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/polylla.h"
@@ -12,12 +13,14 @@ using namespace polylla;
 
 namespace {
 
-constexpr int kStages = 10;
+constexpr int kCore = 10;    // the method's stages, on one mesh or a batch's union
+constexpr int kStages = 12;  // + batch packing and unpacking
 const char *kStageNames[kStages] = {
     "longest_edge", "label_relink", "chords", "chord_links", "cand_count",
-    "cand_scan", "cand_write", "walk", "chunk_scan", "emit",
+    "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack",
 };
-constexpr int kKernels = 11;  // chunk_scan launches two kernels
+constexpr int kKernels = 11;       // chunk_scan launches two kernels
+constexpr int kBatchKernels = 4;   // pack; unpack; ranges (two kernels)
 
 }  // namespace
 
@@ -30,12 +33,22 @@ struct polylla_ctx {
     DevCtrl *h_ctrl = nullptr;      // pinned readback of the control block
     cudaError_t last_cuda = cudaSuccess;
     bool timing = false;
-    cudaEvent_t ev[kStages + 1]{};
+    cudaEvent_t ev_begin[kStages]{}, ev_end[kStages]{};
+    bool stage_ran[kStages]{};
     bool timed_last = false;
     int launches = 0;
     cudaStream_t last_stream = nullptr;
+    // batch: c->mesh is the union, bv the caller's local arrays
+    bool is_batch = false;
+    BatchView bv{};
+    int32_t *poly_off = nullptr;    // [n+1] first polygon of each mesh
+    int32_t *u_origin = nullptr, *u_twin = nullptr;  // union arrays, owned
+    // captured generate (polylla_capture_graph)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_launches = 0;
     // device allocations (for destroy)
-    void *allocs[32]{};
+    void *allocs[64]{};
     int n_allocs = 0;
 };
 
@@ -52,20 +65,31 @@ static int cuda_fail(polylla_ctx *c, cudaError_t e) {
 
 static int dev_alloc(polylla_ctx *c, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
+    if (c->n_allocs >= (int)(sizeof(c->allocs) / sizeof(c->allocs[0]))) return POLYLLA_ERR_OUT_OF_MEMORY;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->allocs[c->n_allocs++] = *p;
     return POLYLLA_OK;
 }
 
+static void drop_graph(polylla_ctx *c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_launches = 0;
+}
+
 static void free_all(polylla_ctx *c) {
+    drop_graph(c);
     for (int i = 0; i < c->n_allocs; i++) cudaFree(c->allocs[i]);
     c->n_allocs = 0;
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
     c->h_ctrl = nullptr;
-    for (int i = 0; i <= kStages; i++) {
-        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-        c->ev[i] = nullptr;
+    for (int i = 0; i < kStages; i++) {
+        if (c->ev_begin[i]) cudaEventDestroy(c->ev_begin[i]);
+        if (c->ev_end[i]) cudaEventDestroy(c->ev_end[i]);
+        c->ev_begin[i] = c->ev_end[i] = nullptr;
     }
 }
 
@@ -76,6 +100,68 @@ static int check_sizes(int32_t V, int32_t T, int32_t H) {
     if ((int64_t)T * 3 >= (int64_t)INT32_MAX) return POLYLLA_ERR_INVALID_ARGUMENT;
     if ((int64_t)H < 3 * (int64_t)T + 3) return POLYLLA_ERR_INVALID_ARGUMENT;
     return POLYLLA_OK;
+}
+
+// ---- launch tuning ----------------------------------------------------------
+// Launch settings that do not change results: the relink block size and the
+// grids of the persistent longest-edge, walk and emit kernels.  A process-
+// wide table keeps the settings polylla_autotune found per device and size
+// bucket (floor(log2 T)); contexts created later for a mesh or batch in a
+// tuned bucket start from them.
+namespace {
+constexpr int kTuneDevices = 16;
+constexpr int kTuneBuckets = 32;
+struct TuneEntry {
+    bool set;
+    polylla_tuning t;
+};
+TuneEntry g_tune[kTuneDevices][kTuneBuckets];
+std::mutex g_tune_lock;
+
+int size_bucket(int32_t T) {
+    int b = 0;
+    while (T > 1 && b < kTuneBuckets - 1) {
+        T >>= 1;
+        b++;
+    }
+    return b;
+}
+}  // namespace
+
+static int sm_count(polylla_ctx *c) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
+    return sms;
+}
+
+static bool tuning_valid(polylla_ctx *c, const polylla_tuning &t) {
+    const int cap = 64 * sm_count(c);
+    auto in = [&](int32_t v) { return v >= 1 && v <= cap; };
+    return (t.relink_threads == 64 || t.relink_threads == 128 || t.relink_threads == 256) &&
+           in(t.longest_edge_blocks) && in(t.walk_blocks) && in(t.emit_blocks);
+}
+
+static void apply_tuning(polylla_ctx *c, const polylla_tuning &t) {
+    c->w.rl_threads = t.relink_threads;
+    c->w.le_blocks = t.longest_edge_blocks;
+    c->w.walk_blocks = t.walk_blocks;
+    c->w.emit_blocks = t.emit_blocks;
+}
+
+static polylla_tuning current_tuning(const polylla_ctx *c) {
+    polylla_tuning t;
+    t.relink_threads = c->w.rl_threads;
+    t.longest_edge_blocks = c->w.le_blocks;
+    t.walk_blocks = c->w.walk_blocks;
+    t.emit_blocks = c->w.emit_blocks;
+    return t;
+}
+
+static void apply_cached_tuning(polylla_ctx *c) {
+    if (c->device < 0 || c->device >= kTuneDevices) return;
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    const TuneEntry &e = g_tune[c->device][size_bucket(c->mesh.T)];
+    if (e.set && tuning_valid(c, e.t)) apply_tuning(c, e.t);
 }
 
 // allocate scratch and outputs for the sizes in c->mesh
@@ -132,10 +218,13 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
     c->w.walk_blocks = 8 * (sms > 0 ? sms : 1);
     c->w.emit_blocks = emit_blocks_per_sm() * (sms > 0 ? sms : 1);
+    c->w.rl_threads = RL_THREADS;
     if (polygons_configure() != 0) return cuda_fail(c, cudaGetLastError());
     c->w.max_rot = (opt && opt->max_rotation > 0) ? opt->max_rotation : 4096;
-    for (int i = 0; i <= kStages; i++) {
-        e = cudaEventCreate(&c->ev[i]);
+    apply_cached_tuning(c);
+    for (int i = 0; i < kStages; i++) {
+        e = cudaEventCreate(&c->ev_begin[i]);
+        if (e == cudaSuccess) e = cudaEventCreate(&c->ev_end[i]);
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
     return POLYLLA_OK;
@@ -233,24 +322,86 @@ int polylla_create_host(polylla_ctx **out, int32_t n_vertices, int32_t n_triangl
     return POLYLLA_OK;
 }
 
-int polylla_generate(polylla_ctx *c, polylla_stream stream) {
-    if (!c) return POLYLLA_ERR_INVALID_ARGUMENT;
-    cudaStream_t s = (cudaStream_t)stream;
-    c->last_stream = s;
-    c->timed_last = c->timing;
-    c->launches = 0;
-    if (c->timing) CK(cudaEventRecord(c->ev[0], s));
-    void (*stages[kStages])(const MeshView &, const Work &, cudaStream_t) = {
+}  // extern "C"
+
+// Enqueue one whole run on s: for a batch, packing, then the method's
+// stages on the union, then unpacking; with timing, an event pair around
+// every stage.
+static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
+    for (int i = 0; i < kStages; i++) c->stage_ran[i] = false;
+    auto begin = [&](int i) -> cudaError_t {
+        c->stage_ran[i] = true;
+        return timing ? cudaEventRecord(c->ev_begin[i], s) : cudaSuccess;
+    };
+    auto end = [&](int i) -> cudaError_t { return timing ? cudaEventRecord(c->ev_end[i], s) : cudaSuccess; };
+    if (c->is_batch) {
+        CK(begin(10));
+        launch_batch_pack(c->bv, c->u_origin, c->u_twin, nullptr, nullptr, nullptr, s);
+        CK(end(10));
+    }
+    void (*stages[kCore])(const MeshView &, const Work &, cudaStream_t) = {
         launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links,
         launch_cand_count, launch_cand_scan, launch_cand_write, launch_walk,
         launch_chunk_scan, launch_emit,
     };
-    for (int i = 0; i < kStages; i++) {
+    for (int i = 0; i < kCore; i++) {
+        CK(begin(i));
         stages[i](c->mesh, c->w, s);
-        if (c->timing) CK(cudaEventRecord(c->ev[i + 1], s));
+        CK(end(i));
     }
-    c->launches = kKernels;
+    if (c->is_batch) {
+        CK(begin(11));
+        launch_batch_unpack(c->bv, c->mesh, s);
+        launch_batch_ranges(c->bv, c->w, c->poly_off, s);
+        CK(end(11));
+    }
+    c->launches = kKernels + (c->is_batch ? kBatchKernels : 0);
     CK(cudaGetLastError());
+    return POLYLLA_OK;
+}
+
+extern "C" {
+
+int polylla_generate(polylla_ctx *c, polylla_stream stream) {
+    if (!c) return POLYLLA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    if (c->graph_exec) {
+        c->timed_last = false;
+        CK(cudaGraphLaunch(c->graph_exec, s));
+        c->launches = c->graph_launches;
+        return POLYLLA_OK;
+    }
+    c->timed_last = c->timing;
+    return enqueue(c, s, c->timing);
+}
+
+int polylla_capture_graph(polylla_ctx *c, polylla_stream stream) {
+    if (!c || !stream) return POLYLLA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    drop_graph(c);
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue(c, s, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : cuda_fail(c, e);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        c->graph_exec = nullptr;
+        return cuda_fail(c, ei);
+    }
+    c->graph = g;
+    c->graph_launches = c->launches;
+    return POLYLLA_OK;
+}
+
+int polylla_release_graph(polylla_ctx *c) {
+    if (!c) return POLYLLA_ERR_INVALID_ARGUMENT;
+    drop_graph(c);
     return POLYLLA_OK;
 }
 
@@ -347,11 +498,15 @@ int polylla_set_timing(polylla_ctx *c, int32_t enable) {
 int polylla_get_stage_times(polylla_ctx *c, float *ms, int32_t n) {
     if (!c || !ms || n < 0) return POLYLLA_ERR_INVALID_ARGUMENT;
     if (!c->timed_last) return 0;
-    CK(cudaEventSynchronize(c->ev[kStages]));
-    int k = n < kStages ? n : kStages;
+    int last = -1;
+    for (int i = 0; i < kStages; i++)
+        if (c->stage_ran[i]) last = i;
+    if (last < 0) return 0;
+    CK(cudaEventSynchronize(c->ev_end[c->is_batch ? 11 : kCore - 1]));
+    const int k = n < kStages ? n : kStages;
     for (int i = 0; i < k; i++) {
         float t = 0.f;
-        CK(cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+        if (c->stage_ran[i]) CK(cudaEventElapsedTime(&t, c->ev_begin[i], c->ev_end[i]));
         ms[i] = t;
     }
     return k;
@@ -368,6 +523,210 @@ void polylla_destroy(polylla_ctx *c) {
     cudaDeviceSynchronize();
     free_all(c);
     delete c;
+}
+
+// ---- batches ------------------------------------------------------------------
+
+int polylla_batch_create(polylla_ctx **out, const polylla_batch *b, const polylla_options *opt,
+                         polylla_stream stream) {
+    if (!out) return POLYLLA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (!b || b->n_meshes < 1 || !b->vertex_offset || !b->triangle_offset || !b->halfedge_offset)
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    if (!b->coords || !b->origin || !b->twin || !b->next || !b->prev) return POLYLLA_ERR_INVALID_ARGUMENT;
+    if (!aligned(b->coords, 16) || !aligned(b->origin, 4) || !aligned(b->twin, 4) || !aligned(b->next, 4) ||
+        !aligned(b->prev, 4))
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    const int32_t n = b->n_meshes;
+    const int32_t *vo = b->vertex_offset, *to = b->triangle_offset, *ho = b->halfedge_offset;
+    if (vo[0] != 0 || to[0] != 0 || ho[0] != 0) return POLYLLA_ERR_INVALID_ARGUMENT;
+    for (int32_t i = 0; i < n; i++) {
+        const int64_t Vi = (int64_t)vo[i + 1] - vo[i], Ti = (int64_t)to[i + 1] - to[i], Hi = (int64_t)ho[i + 1] - ho[i];
+        if (Vi < 3 || Ti < 1 || Hi < 3 * Ti + 3) return POLYLLA_ERR_INVALID_ARGUMENT;
+    }
+    int rc = check_sizes(vo[n], to[n], ho[n]);
+    if (rc) return rc;
+    polylla_ctx *c = new (std::nothrow) polylla_ctx();
+    if (!c) return POLYLLA_ERR_OUT_OF_MEMORY;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return POLYLLA_ERR_CUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    c->is_batch = true;
+    const int32_t V = vo[n], T = to[n], H = ho[n];
+    c->mesh.V = V;
+    c->mesh.T = T;
+    c->mesh.H = H;
+    c->mesh.xy = reinterpret_cast<const double2 *>(b->coords);
+    BatchView &bv = c->bv;
+    bv.n = n;
+    bv.T_tot = T;
+    bv.H_tot = H;
+    bv.origin = b->origin;
+    bv.twin = b->twin;
+    bv.next = b->next;
+    bv.prev = b->prev;
+    void *p = nullptr;
+    int32_t *d_off[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4 && !rc; k++)
+        if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(n + 1))) == 0) d_off[k] = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(n + 1))) == 0) c->poly_off = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_origin = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_twin = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.next = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.prev = (int32_t *)p;
+    if (!rc) {
+        c->mesh.origin = c->u_origin;
+        c->mesh.twin = c->u_twin;
+        // border prefix sums b_off[i] = h_off[i] - 3 t_off[i]
+        int32_t *h_b = new (std::nothrow) int32_t[(size_t)n + 1];
+        if (!h_b) rc = POLYLLA_ERR_OUT_OF_MEMORY;
+        else {
+            for (int32_t i = 0; i <= n; i++) h_b[i] = ho[i] - 3 * to[i];
+            const int32_t *src[4] = {vo, to, ho, h_b};
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < 4 && e == cudaSuccess; k++)
+                e = cudaMemcpy(d_off[k], src[k], sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice);
+            delete[] h_b;
+            if (e != cudaSuccess) rc = cuda_fail(c, e);
+        }
+    }
+    if (!rc) {
+        bv.v_off = d_off[0];
+        bv.t_off = d_off[1];
+        bv.h_off = d_off[2];
+        bv.b_off = d_off[3];
+        rc = alloc_work(c, opt);
+    }
+    if (!rc) {
+        c->w.loc_t_off = bv.t_off;
+        c->w.loc_v_off = bv.v_off;
+        c->w.loc_n = n;
+        if (!opt || opt->validate) {
+            // range checks of every local index while packing all four
+            // arrays, then the single-mesh layout check on the union
+            cudaError_t e = cudaMemsetAsync(c->d_bad, 0, sizeof(int32_t), s);
+            if (e == cudaSuccess) {
+                launch_batch_pack(bv, c->u_origin, c->u_twin, c->mesh.next, c->mesh.prev, c->d_bad, s);
+                e = cudaGetLastError();
+            }
+            int32_t bad = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_fail(c, e);
+            else if (bad) rc = POLYLLA_ERR_INVALID_MESH;
+            else rc = run_validate(c, s);
+        }
+    }
+    if (rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return POLYLLA_OK;
+}
+
+int polylla_batch_polygon_offsets(polylla_ctx *c, const int32_t **poly_offset) {
+    if (!c || !poly_offset || !c->is_batch) return POLYLLA_ERR_INVALID_ARGUMENT;
+    *poly_offset = c->poly_off;
+    return POLYLLA_OK;
+}
+
+// ---- tuning -------------------------------------------------------------------
+
+int polylla_get_tuning(polylla_ctx *c, polylla_tuning *out) {
+    if (!c || !out) return POLYLLA_ERR_INVALID_ARGUMENT;
+    *out = current_tuning(c);
+    return POLYLLA_OK;
+}
+
+int polylla_set_tuning(polylla_ctx *c, const polylla_tuning *t) {
+    if (!c || !t || !tuning_valid(c, *t)) return POLYLLA_ERR_INVALID_ARGUMENT;
+    drop_graph(c);
+    apply_tuning(c, *t);
+    return POLYLLA_OK;
+}
+
+int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_stream stream) {
+    if (!c || reps < 1) return POLYLLA_ERR_INVALID_ARGUMENT;
+    drop_graph(c);
+    const bool timing = c->timing;
+    c->timing = true;
+    const int sms = sm_count(c);
+    // median time of one stage over reps whole runs
+    auto stage_ms = [&](int stage, float *med) -> int {
+        float v[64];
+        const int r = reps < 64 ? reps : 64;
+        for (int i = 0; i < r; i++) {
+            int rc = polylla_generate(c, stream);
+            if (rc) return rc;
+            float ms[kStages];
+            if (polylla_get_stage_times(c, ms, kStages) != kStages) return POLYLLA_ERR_CUDA;
+            v[i] = ms[stage];
+        }
+        for (int i = 1; i < r; i++)  // insertion sort, r is small
+            for (int j = i; j > 0 && v[j] < v[j - 1]; j--) {
+                float t = v[j];
+                v[j] = v[j - 1];
+                v[j - 1] = t;
+            }
+        *med = v[r / 2];
+        return POLYLLA_OK;
+    };
+    struct Knob {
+        int stage;
+        int32_t *field;
+        int32_t cand[8];
+        int n;
+    };
+    const int le_occ = longest_edge_blocks_per_sm(), em_occ = emit_blocks_per_sm();
+    Knob knobs[4] = {
+        {1, &c->w.rl_threads, {64, 128, 256}, 3},
+        {0, &c->w.le_blocks, {0}, 0},
+        {7, &c->w.walk_blocks, {2 * sms, 4 * sms, 8 * sms, 16 * sms}, 4},
+        {9, &c->w.emit_blocks, {0}, 0},
+    };
+    for (int k = 1; k <= le_occ && knobs[1].n < 8; k++) knobs[1].cand[knobs[1].n++] = k * sms;
+    for (int k = 1; k <= em_occ && knobs[3].n < 8; k++) knobs[3].cand[knobs[3].n++] = k * sms;
+    int rc = POLYLLA_OK;
+    for (int q = 0; q < 4 && !rc; q++) {
+        Knob &kb = knobs[q];
+        int32_t best = *kb.field;
+        float best_ms = 0.f;
+        rc = stage_ms(kb.stage, &best_ms);
+        for (int i = 0; i < kb.n && !rc; i++) {
+            if (kb.cand[i] == best) continue;
+            const int32_t keep = *kb.field;
+            *kb.field = kb.cand[i];
+            float t = 0.f;
+            rc = stage_ms(kb.stage, &t);
+            if (!rc && t < best_ms) {
+                best_ms = t;
+                best = kb.cand[i];
+            } else {
+                *kb.field = keep;
+            }
+        }
+        *kb.field = best;
+    }
+    c->timing = timing;
+    if (rc) return rc;
+    const polylla_tuning t = current_tuning(c);
+    if (c->device >= 0 && c->device < kTuneDevices) {
+        std::lock_guard<std::mutex> g(g_tune_lock);
+        g_tune[c->device][size_bucket(c->mesh.T)] = TuneEntry{true, t};
+    }
+    if (out) *out = t;
+    return POLYLLA_OK;
+}
+
+int polylla_tuning_cache_clear(void) {
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    for (int d = 0; d < kTuneDevices; d++)
+        for (int b = 0; b < kTuneBuckets; b++) g_tune[d][b].set = false;
+    return POLYLLA_OK;
 }
 
 }  // extern "C"

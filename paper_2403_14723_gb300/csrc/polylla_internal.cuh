@@ -63,6 +63,7 @@ struct Work {
     int32_t n_cc_blocks;            // ceil(T / CC_TRI)
     int32_t n_chunk_max;            // ceil(3T / CHUNK)
     int32_t walk_blocks, emit_blocks;
+    int32_t rl_threads;             // relink block size: 64, 128 or 256
     int32_t *seeds;
     int32_t *offsets;
     int32_t *he_list;
@@ -71,6 +72,28 @@ struct Work {
     int32_t max_rot;
     int32_t persistent_blocks;   // grid of the sparse (tip) kernels
     int32_t le_blocks;           // grid of the persistent longest-edge kernel
+    // batches: the emitted he_list / v_list are made mesh-local when set
+    const int32_t *loc_t_off;    // [loc_n+1] triangle offset of each mesh
+    const int32_t *loc_v_off;    // [loc_n+1] vertex offset of each mesh
+    int32_t loc_n;               // number of meshes (0: a single mesh)
+};
+
+// A batch of independent meshes, each in the single-mesh layout with its own
+// (local) indices, concatenated; prefix sums locate mesh i.  The kernels run
+// on the batch's union: one mesh whose interior half-edges are those of all
+// meshes in order ([3 t_off[i], 3 t_off[i+1]) for mesh i), followed by all
+// border half-edges ([3 T_tot + b_off[i], ...)), with global vertex ids.
+struct BatchView {
+    int32_t n;                   // meshes
+    int32_t T_tot, H_tot;
+    const int32_t *v_off;        // [n+1] device prefix sums of V_i
+    const int32_t *t_off;        // [n+1] of T_i
+    const int32_t *h_off;        // [n+1] of H_i
+    const int32_t *b_off;        // [n+1] of H_i - 3 T_i (border half-edges)
+    const int32_t *origin;       // local arrays [sum H_i]
+    const int32_t *twin;
+    int32_t *next;
+    int32_t *prev;
 };
 
 // output kernels: start counting/compaction over blocks of CC_TRI
@@ -90,7 +113,7 @@ constexpr int EMIT_BUF = 256;  // CSR entries staged per warp
 constexpr int LE_THREADS = 256;
 constexpr int LE_TILE = 64;
 
-// relink kernel: one thread per triangle
+// relink kernel: one thread per triangle, 64, 128 (default) or 256 per block
 constexpr int RL_THREADS = 128;
 
 // bounded waits: iterations of an mbarrier try_wait loop before giving up
@@ -139,6 +162,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+// largest i in [0, n) with off[i] <= x, for ascending prefix sums off[0..n]
+// with off[0] <= x < off[n]
+__device__ __forceinline__ int32_t seg_of(const int32_t *off, int32_t n, int32_t x) {
+    int32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---- implicit triangle layout (paper Section 4.2) -------------------------
 __device__ __forceinline__ int32_t tri_of(int32_t e) { return e / 3; }
 __device__ __forceinline__ int32_t loc_of(int32_t e) { return e - 3 * (e / 3); }
@@ -168,5 +203,10 @@ void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);  // tw
 void launch_emit(const MeshView &m, const Work &w, cudaStream_t s);
 int polygons_configure();
 int emit_blocks_per_sm();
+// batches (kernels_batch.cu)
+void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
+                       int32_t *bad, cudaStream_t s);
+void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s);
+void launch_batch_ranges(const BatchView &b, const Work &w, int32_t *poly_off, cudaStream_t s);  // two kernels
 
 }  // namespace polylla

@@ -125,6 +125,7 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
     w.walk_blocks = 8 * (sms > 0 ? sms : 1);
     w.emit_blocks = emit_blocks_per_sm() * (sms > 0 ? sms : 1);
+    w.rl_threads = RL_THREADS;
 
     // The first kernel zeroes the control block and k_cand_count zeroes the
     // chunk totals; every other scratch word is written before it is read,

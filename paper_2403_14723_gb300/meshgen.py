@@ -391,6 +391,42 @@ WORKLOADS = {
 }
 
 
+def batch_sizes(n_meshes: int, t_min: int, t_max: int, seed: int) -> np.ndarray:
+    """Target triangle counts, log-uniform in ``[t_min, t_max]``."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(t_min), np.log(t_max), size=n_meshes)).round().astype(np.int64)
+
+
+def batch_member(i: int, t_target: int, seed: int) -> HalfEdgeMesh:
+    """Mesh ``i`` of a batch: even ``i`` Delaunay of uniform random points
+    (about ``t_target / 2`` points), odd ``i`` a perturbed grid (jitter 0.3,
+    about ``sqrt(t_target / 2) + 1`` vertices a side); seed ``seed + i``."""
+    if i % 2 == 0:
+        return random_delaunay(max(4, int(round(t_target / 2)) + 1), seed=seed + i)
+    s = max(2, int(round(np.sqrt(t_target / 2.0))) + 1)
+    return perturbed_grid(s, 0.3, seed=seed + i)
+
+
+def _batch_member_args(args):
+    return batch_member(*args)
+
+
+def random_batch(n_meshes: int = 4096, t_min: int = 100, t_max: int = 200_000, seed: int = 4,
+                 workers: int = 0) -> list[HalfEdgeMesh]:
+    """A batch of independent triangulations: sizes log-uniform in
+    ``[t_min, t_max]`` triangles, alternately Delaunay and perturbed grids.
+    ``workers > 1`` builds the meshes in a spawned process pool."""
+    sizes = batch_sizes(n_meshes, t_min, t_max, seed)
+    args = [(i, int(t), seed) for i, t in enumerate(sizes)]
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batch_member_args, args, chunksize=16))
+    return [batch_member(*a) for a in args]
+
+
 def workload(name: str) -> HalfEdgeMesh:
     """Build one of the named synthetic workloads."""
     if name in WORKLOADS:

@@ -68,6 +68,22 @@ class polylla_host_result(ctypes.Structure):
                 ("n_polygons", ctypes.c_int32), ("n_frontier", ctypes.c_int32)]
 
 
+class polylla_batch(ctypes.Structure):
+    _fields_ = [("n_meshes", ctypes.c_int32),
+                ("vertex_offset", ctypes.c_void_p), ("triangle_offset", ctypes.c_void_p),
+                ("halfedge_offset", ctypes.c_void_p),
+                ("coords", ctypes.c_void_p), ("origin", ctypes.c_void_p), ("twin", ctypes.c_void_p),
+                ("next", ctypes.c_void_p), ("prev", ctypes.c_void_p)]
+
+
+class polylla_tuning(ctypes.Structure):
+    _fields_ = [("relink_threads", ctypes.c_int32), ("longest_edge_blocks", ctypes.c_int32),
+                ("walk_blocks", ctypes.c_int32), ("emit_blocks", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 # every function the header declares, with its ctypes signature
 _SIGNATURES = {
     "polylla_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_mesh),
@@ -91,6 +107,16 @@ _SIGNATURES = {
     "polylla_generate_noalloc": (ctypes.c_int, [ctypes.POINTER(polylla_mesh), ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
+    "polylla_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_batch),
+                                            ctypes.POINTER(polylla_options), ctypes.c_void_p]),
+    "polylla_batch_polygon_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "polylla_capture_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polylla_release_graph": (ctypes.c_int, [ctypes.c_void_p]),
+    "polylla_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_tuning)]),
+    "polylla_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_tuning)]),
+    "polylla_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(polylla_tuning),
+                                        ctypes.c_void_p]),
+    "polylla_tuning_cache_clear": (ctypes.c_int, []),
 }
 
 _lib = None
@@ -320,6 +346,108 @@ def polylla_generate_noalloc(mesh: DeviceMesh, seeds, offsets, he_list, v_list, 
         if not t.is_cuda or t.dtype != torch.int32 or t.numel() < n:
             raise ValueError(f"device int32 tensor of at least {n} elements expected")
     _check(lib.polylla_generate_noalloc(ctypes.byref(m), *ptrs, _stream_ptr(stream)), "polylla_generate_noalloc")
+
+
+def polylla_capture_graph(ctx: int, stream=None) -> None:
+    """Record one generate into a CUDA graph that later generates launch
+    (the stream must be a non-default torch stream)."""
+    _check(load_library().polylla_capture_graph(ctypes.c_void_p(ctx), _stream_ptr(stream)), "polylla_capture_graph")
+
+
+def polylla_release_graph(ctx: int) -> None:
+    _check(load_library().polylla_release_graph(ctypes.c_void_p(ctx)), "polylla_release_graph")
+
+
+def polylla_get_tuning(ctx: int) -> dict:
+    t = polylla_tuning()
+    _check(load_library().polylla_get_tuning(ctypes.c_void_p(ctx), ctypes.byref(t)), "polylla_get_tuning")
+    return t.as_dict()
+
+
+def polylla_set_tuning(ctx: int, tuning: dict) -> None:
+    t = polylla_tuning(**{k: int(v) for k, v in tuning.items()})
+    _check(load_library().polylla_set_tuning(ctypes.c_void_p(ctx), ctypes.byref(t)), "polylla_set_tuning")
+
+
+def polylla_autotune(ctx: int, reps: int = 5, stream=None) -> dict:
+    t = polylla_tuning()
+    _check(load_library().polylla_autotune(ctypes.c_void_p(ctx), int(reps), ctypes.byref(t), _stream_ptr(stream)),
+           "polylla_autotune")
+    return t.as_dict()
+
+
+def polylla_tuning_cache_clear() -> None:
+    _check(load_library().polylla_tuning_cache_clear(), "polylla_tuning_cache_clear")
+
+
+@dataclass
+class DeviceBatch:
+    """Concatenated device arrays of a batch of meshes plus host prefix sums
+    (see ``polylla_batch`` in the header)."""
+
+    coords: "object"           # [V_total, 2] float64
+    origin: "object"           # [H_total] int32, local indices per mesh
+    twin: "object"
+    next: "object"
+    prev: "object"
+    vertex_offset: "object"    # host numpy int32 [n+1]
+    triangle_offset: "object"
+    halfedge_offset: "object"
+
+    @property
+    def n_meshes(self) -> int:
+        return len(self.triangle_offset) - 1
+
+    @classmethod
+    def from_host(cls, meshes, device="cuda"):
+        """Concatenate host meshes (``meshgen.HalfEdgeMesh``) into one batch."""
+        import numpy as np
+        import torch
+
+        def cat(name):
+            return torch.from_numpy(np.concatenate([getattr(m, name) for m in meshes])).to(device).contiguous()
+
+        def prefix(vals):
+            out = np.zeros(len(vals) + 1, dtype=np.int64)
+            np.cumsum(vals, out=out[1:])
+            if out[-1] >= 2 ** 31:
+                raise ValueError("batch exceeds int32 indexing")
+            return out.astype(np.int32)
+
+        return cls(coords=cat("coords"), origin=cat("origin"), twin=cat("twin"), next=cat("next"), prev=cat("prev"),
+                   vertex_offset=prefix([m.n_vertices for m in meshes]),
+                   triangle_offset=prefix([m.n_triangles for m in meshes]),
+                   halfedge_offset=prefix([m.n_halfedges for m in meshes]))
+
+
+def polylla_batch_create(batch: DeviceBatch, validate: bool = True, max_rotation: int = 0, stream=None) -> int:
+    import numpy as np
+    import torch
+
+    lib = load_library()
+    V = int(batch.vertex_offset[-1])
+    H = int(batch.halfedge_offset[-1])
+    offs = [np.ascontiguousarray(a, dtype=np.int32) for a in
+            (batch.vertex_offset, batch.triangle_offset, batch.halfedge_offset)]
+    b = polylla_batch(batch.n_meshes, *(ctypes.c_void_p(a.ctypes.data) for a in offs),
+                      _dev_ptr(batch.coords.view(-1), torch.float64, 2 * V),
+                      _dev_ptr(batch.origin, torch.int32, H), _dev_ptr(batch.twin, torch.int32, H),
+                      _dev_ptr(batch.next, torch.int32, H), _dev_ptr(batch.prev, torch.int32, H))
+    opt = polylla_options(1 if validate else 0, int(max_rotation))
+    ctx = ctypes.c_void_p()
+    _check(lib.polylla_batch_create(ctypes.byref(ctx), ctypes.byref(b), ctypes.byref(opt), _stream_ptr(stream)),
+           "polylla_batch_create")
+    return ctx.value
+
+
+def polylla_batch_polygon_offsets(ctx: int, n_meshes: int):
+    """Device int32 view [n+1]: mesh i owns polygons [off[i], off[i+1])."""
+    import torch
+
+    p = ctypes.c_void_p()
+    _check(load_library().polylla_batch_polygon_offsets(ctypes.c_void_p(ctx), ctypes.byref(p)),
+           "polylla_batch_polygon_offsets")
+    return _view(p.value, n_meshes + 1, "<i4", torch.int32)
 
 
 class Polylla:

@@ -5,6 +5,8 @@ import os
 import re
 import subprocess
 
+import numpy as np
+
 import pytest
 
 from paper_2403_14723_gb300 import build, polylla
@@ -47,10 +49,10 @@ def test_status_strings_without_gpu(lib_path):
     lib = polylla.load_library()
     assert lib.polylla_status_string(0) == b"ok"
     assert lib.polylla_status_string(-2) == b"invalid mesh layout"
-    assert lib.polylla_stage_count() == 10
-    names = [lib.polylla_stage_name(i).decode() for i in range(10)]
+    assert lib.polylla_stage_count() == 12
+    names = [lib.polylla_stage_name(i).decode() for i in range(12)]
     assert names == ["longest_edge", "label_relink", "chords", "chord_links", "cand_count",
-                     "cand_scan", "cand_write", "walk", "chunk_scan", "emit"]
+                     "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack"]
 
 
 def test_null_arguments_rejected_without_gpu(lib_path):
@@ -62,6 +64,17 @@ def test_null_arguments_rejected_without_gpu(lib_path):
     assert lib.polylla_create(ctypes.byref(ctx), ctypes.byref(m), None, None) == -1
     assert lib.polylla_generate(None, None) == -1
     assert lib.polylla_get_polygons(None, None, None) == -1
+    assert lib.polylla_batch_create(None, None, None, None) == -1
+    assert lib.polylla_batch_create(ctypes.byref(ctx), None, None, None) == -1
+    one = np.array([0, 3], dtype=np.int32)
+    zero_t = np.array([0, 0], dtype=np.int32)                          # a mesh without triangles
+    b = polylla.polylla_batch(1, one.ctypes.data, zero_t.ctypes.data, one.ctypes.data, 16, 16, 16, 16, 16)
+    assert lib.polylla_batch_create(ctypes.byref(ctx), ctypes.byref(b), None, None) == -1
+    assert lib.polylla_capture_graph(None, None) == -1
+    assert lib.polylla_autotune(None, 1, None, None) == -1
+    assert lib.polylla_set_tuning(None, None) == -1
+    assert lib.polylla_batch_polygon_offsets(None, None) == -1
+    assert lib.polylla_tuning_cache_clear() == 0
 
 
 def test_built_for_sm_103a_only():
