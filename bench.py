@@ -10,6 +10,7 @@ workload is the largest single mesh: the 4096 x 4096 perturbed grid
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle, timed on the host
     python bench.py --workload batch_4096  # 4,096 meshes in one batched run
+    python bench.py --workload served      # Poisson request stream, continuous batching
 
 The batched workload (4,096 independent triangulations, sizes log-uniform in
 [100, 200,000] triangles, alternately Delaunay and perturbed grids) runs
@@ -51,6 +52,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the served request trace (served workload)")
+    ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
+                    help="trace length replayed through the one-mesh-at-a-time server")
     return ap.parse_args()
 
 
@@ -225,6 +230,14 @@ def algorithmic_bytes(T, V, NF, P):
 def ref_sample_mesh(workload: str):
     from paper_2403_14723_gb300 import meshgen
 
+    if workload == "served":
+        # the first 64 small and 2 large meshes of the request pool's recipe
+        r = SERVE_RECIPE
+        small = meshgen.batch_sizes(r["pool_small"], *r["small"], seed=r["seed"])[:64]
+        large = meshgen.batch_sizes(r["pool_large"], *r["large"], seed=r["seed"] + 1)[:2]
+        ms = [meshgen.batch_member(i, int(t), 10_000 + r["seed"]) for i, t in enumerate(small)]
+        ms += [meshgen.batch_member(i, int(t), 20_000 + r["seed"]) for i, t in enumerate(large)]
+        return ms, f"64 small + 2 large meshes of the request pool ({sum(m.n_triangles for m in ms):,} triangles)"
     if workload.startswith("batch_"):
         # the first 64 meshes of the batch recipe; the oracle runs them one by one
         r = BATCH_RECIPE
@@ -610,12 +623,134 @@ def run_batched(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# served workload: Poisson request stream through the serving loop
+# ---------------------------------------------------------------------------
+
+SERVE_RECIPE = {"rate": 2000.0, "small": (1_000, 50_000), "large": (500_000, 8_000_000), "p_large": 0.2,
+                "pool_small": 512, "pool_large": 32, "budget": 40 << 30, "seed": 5}
+
+
+def serve_pool():
+    """Seeded pool of request meshes: sizes log-uniform per band, Delaunay
+    and perturbed grids alternately (built in a spawned process pool)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from paper_2403_14723_gb300 import meshgen
+
+    r = SERVE_RECIPE
+    small = meshgen.batch_sizes(r["pool_small"], *r["small"], seed=r["seed"])
+    large = meshgen.batch_sizes(r["pool_large"], *r["large"], seed=r["seed"] + 1)
+    args = [(i, int(t), 10_000 + r["seed"]) for i, t in enumerate(small)]
+    args += [(i, int(t), 20_000 + r["seed"]) for i, t in enumerate(large)]
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        meshes = list(ex.map(meshgen._batch_member_args, args, chunksize=4))
+    return meshes[: len(small)], meshes[len(small):]
+
+
+def serve_trace(seconds: float, n_small: int, n_large: int, seed: int):
+    """Poisson arrivals at the recipe's rate; each request picks a small
+    pool mesh (80 %) or a large one (20 %)."""
+    import numpy as np
+
+    r = SERVE_RECIPE
+    rng = np.random.default_rng(seed)
+    n = int(r["rate"] * seconds * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / r["rate"], size=n))
+    t = t[t < seconds]
+    large = rng.random(len(t)) < r["p_large"]
+    pick = np.where(large, n_small + rng.integers(0, n_large, len(t)), rng.integers(0, n_small, len(t)))
+    return t, pick
+
+
+def run_served(args):
+    small, large = serve_pool()               # process pool, before any CUDA call
+    import numpy as np
+    import torch
+
+    from paper_2403_14723_gb300 import build, polylla
+
+    rank, ws, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(torch.device("cuda", local))
+    build.build_library()
+    pool = small + large
+    hrs = [polylla.HostRequest(m) for m in pool]
+    tri = np.array([m.n_triangles for m in pool], dtype=np.int64)
+    r = SERVE_RECIPE
+
+    def replay(srv, seconds, seed):
+        t, pick = serve_trace(seconds, len(small), len(large), seed)
+        rc, lat, infos = srv.replay([hrs[i] for i in pick], t)
+        assert rc == 0, f"served requests failed: {polylla.STATUS.get(rc, rc)}"
+        span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        return {"requests": len(t), "triangles": int(tri[pick].sum()), "span_s": span,
+                "tri_per_s": float(tri[pick].sum()) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_batch": float(np.mean([i["batch_meshes"] for i in infos])),
+                "h2d_bytes": int(sum(16 * pool[i].n_vertices + 16 * pool[i].n_halfedges for i in pick)),
+                "d2h_bytes": int(sum(4 * (2 * infos[k]["n_polygons"] + 1 + 2 * infos[k]["n_frontier"] + 2 * pool[i].n_halfedges)
+                                     for k, i in enumerate(pick)))}
+
+    with polylla.Server(memory_budget=r["budget"], n_slots=3) as srv:
+        replay(srv, 1.0, seed=1000 + rank)                     # warm-up, untimed
+        dist_barrier(ws)
+        st0 = srv.stats()
+        with ClockSampler(local) as clk:
+            main = replay(srv, args.serve_seconds, seed=r["seed"] + rank)
+        st = srv.stats()
+    batches = int(st["batches"] - st0["batches"])
+    with polylla.Server(memory_budget=r["budget"], n_slots=1, max_batch_meshes=1) as one:
+        replay(one, 0.5, seed=2000 + rank)
+        base = replay(one, args.serve_baseline_seconds, seed=r["seed"] + rank)
+    value = main["tri_per_s"]
+    if ws > 1:
+        import torch.distributed as dist
+
+        tot = torch.tensor([float(main["triangles"])], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tot)
+        value = float(tot[0]) / dist_max(main["span_s"], ws)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": main["requests"], "warmup": 1,
+            "ms_per_step": 1e3 * main["span_s"] / main["requests"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/int32", "data": "synthetic",
+            "config": {"workload": "served", "rate_req_per_s": r["rate"], "seconds": args.serve_seconds,
+                       "requests": main["requests"], "triangles": main["triangles"],
+                       "mix": f"{int(100 * (1 - r['p_large']))}% log-uniform {r['small']} triangles, "
+                              f"{int(100 * r['p_large'])}% log-uniform {r['large']}; Delaunay and perturbed grids",
+                       "pool": f"{len(small)} small + {len(large)} large seeded meshes in pinned host memory",
+                       "memory_budget_bytes": r["budget"], "slots": st["n_slots"],
+                       "slot_triangles": st["slot_triangles"], "device_bytes": st["device_bytes"],
+                       "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
+            "served": main, "server_stats": st,
+            "one_mesh_at_a_time": dict(base, how="same server loop with one slot and one mesh per batch, "
+                                                  f"{args.serve_baseline_seconds:g} s of the same recipe"),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": main["h2d_bytes"] // max(1, main["requests"]),
+                    "d2h_bytes_per_step": main["d2h_bytes"] // max(1, main["requests"]),
+                    "api": "polylla_server_replay: host meshes in, host results out, per request"},
+            "roofline": None, "cpu_baseline": None,
+            "gpu_launches": batches * 16, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("batch_"):
         return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_gb300(args)
 
 

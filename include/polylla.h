@@ -293,6 +293,75 @@ int polylla_autotune(polylla_ctx *ctx, int32_t reps, polylla_tuning *out, polyll
 int polylla_tuning_cache_clear(void);
 
 /*
+ * Serving (no counterpart in the paper): a request loop with continuous
+ * batching.  Requests are meshes in host memory (pinned for full copy
+ * speed); a scheduler thread owned by the server admits them, in arrival
+ * order, into batches as batch slots and their device memory free up, and
+ * runs each batch as one batched generate (see polylla_batch_create) on the
+ * slot's own stream: copies in, the method, copies out.  Slots overlap on
+ * the device (one copies in while another computes and a third copies
+ * out), and requests that arrive while batches are in flight join the next
+ * batch a slot forms -- no request waits for a fixed batch to fill.
+ *
+ * Memory: the server holds at most memory_budget bytes of device memory,
+ * split into n_slots slots of equal capacity (triangles, vertices, half-
+ * edges, meshes), all allocated at create; a batch is admitted into a slot
+ * only while it fits the slot's capacity.  A request larger than one slot
+ * completes at once with POLYLLA_ERR_TOO_LARGE.
+ *
+ * A request's result is exactly what polylla_generate_host gives for the
+ * mesh alone, whatever it was batched with: CSR and next/prev in the
+ * mesh's own indices, written to the request's host buffers (capacities as
+ * polylla_generate_host).  The host arrays of a request must stay valid
+ * and unchanged until it completes.
+ */
+typedef struct polylla_server polylla_server;
+typedef struct {
+    int64_t memory_budget;     /* device bytes the server may hold (> 0)        */
+    int32_t n_slots;           /* batches in flight, >= 1 (0: 3)                 */
+    int32_t max_batch_meshes;  /* meshes per batch, >= 1 (0: 4096)               */
+    int32_t max_rotation;      /* as polylla_options (0: 4096)                   */
+} polylla_server_options;
+typedef struct {
+    int32_t n_vertices, n_triangles, n_halfedges;
+    polylla_host_mesh mesh;      /* inputs (host)                                  */
+    polylla_host_result result;  /* outputs (host); n_polygons/n_frontier set at completion */
+} polylla_request;
+typedef struct {
+    int32_t status;              /* POLYLLA_OK or the request's error              */
+    int32_t n_polygons, n_frontier;
+    int32_t batch_meshes;        /* meshes in the batch the request ran in         */
+    double t_submit, t_admit, t_done; /* seconds on the server's steady clock      */
+} polylla_request_info;
+typedef struct {
+    int32_t n_slots;
+    int32_t slot_triangles;      /* capacity of one slot                           */
+    int64_t device_bytes;        /* device memory held                             */
+    int64_t batches, requests_done;
+    double busy_seconds;         /* time with at least one batch in flight         */
+} polylla_server_stats;
+
+/* Create a server on the current device (allocates all slots; starts the
+ * scheduler thread).  Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
+int polylla_server_create(polylla_server **out, const polylla_server_options *opt);
+/* Queue a request (the struct is copied; the arrays are not); *ticket
+ * identifies it.  Never blocks on the GPU. */
+int polylla_server_submit(polylla_server *srv, const polylla_request *req, int64_t *ticket);
+/* Block until the ticket's request completes; fill *info (may be NULL) and
+ * forget the ticket.  Returns the request's status. */
+int polylla_server_wait(polylla_server *srv, int64_t ticket, polylla_request_info *info);
+/* Open-loop replay: submit reqs[k] at arrival_s[k] seconds (ascending)
+ * after the call starts, from a native thread, wait for all, and write each
+ * request's latency (completion minus its scheduled arrival) to
+ * latency_s[k] and its info to infos[k] (may be NULL).  Returns the first
+ * failing status, or POLYLLA_OK. */
+int polylla_server_replay(polylla_server *srv, int32_t n, const polylla_request *reqs,
+                          const double *arrival_s, double *latency_s, polylla_request_info *infos);
+int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out);
+/* Finish every queued request, stop the scheduler, free everything. */
+void polylla_server_destroy(polylla_server *srv);
+
+/*
  * polylla_generate_noalloc -- the whole method, allocating nothing.
  *
  * (No counterpart in the paper: this is a deployment convenience.)  For

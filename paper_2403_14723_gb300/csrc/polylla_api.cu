@@ -8,6 +8,7 @@
 
 #include "../../include/polylla.h"
 #include "polylla_internal.cuh"
+#include "polylla_serve.cuh"
 
 using namespace polylla;
 
@@ -43,6 +44,11 @@ struct polylla_ctx {
     BatchView bv{};
     int32_t *poly_off = nullptr;    // [n+1] first polygon of each mesh
     int32_t *u_origin = nullptr, *u_twin = nullptr;  // union arrays, owned
+    // serving: per-mesh metadata and rebased offsets after each run
+    bool serve = false;
+    int32_t *meta = nullptr;           // [4 n_cap]
+    int32_t *local_offsets = nullptr;  // [T_cap + n_cap + 1]
+    size_t bytes = 0;                  // device bytes allocated
     // captured generate (polylla_capture_graph)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -69,6 +75,7 @@ static int dev_alloc(polylla_ctx *c, void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->allocs[c->n_allocs++] = *p;
+    c->bytes += bytes;
     return POLYLLA_OK;
 }
 
@@ -230,6 +237,43 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     return POLYLLA_OK;
 }
 
+// Union arrays, offset arrays and polygon ranges of a batch context for n
+// meshes of V, T, H in total; c->mesh becomes the union view (sizes V, T, H)
+// over the caller's coords.  The offset arrays are left to the caller.
+static int batch_alloc(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const double *coords,
+                       const int32_t *origin, const int32_t *twin, int32_t *next, int32_t *prev) {
+    c->is_batch = true;
+    c->mesh.V = V;
+    c->mesh.T = T;
+    c->mesh.H = H;
+    c->mesh.xy = reinterpret_cast<const double2 *>(coords);
+    BatchView &bv = c->bv;
+    bv.n = n;
+    bv.T_tot = T;
+    bv.H_tot = H;
+    bv.origin = origin;
+    bv.twin = twin;
+    bv.next = next;
+    bv.prev = prev;
+    int rc = POLYLLA_OK;
+    void *p = nullptr;
+    int32_t *d_off[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4 && !rc; k++)
+        if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(n + 1))) == 0) d_off[k] = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(n + 1))) == 0) c->poly_off = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_origin = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_twin = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.next = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.prev = (int32_t *)p;
+    c->mesh.origin = c->u_origin;
+    c->mesh.twin = c->u_twin;
+    bv.v_off = d_off[0];
+    bv.t_off = d_off[1];
+    bv.h_off = d_off[2];
+    bv.b_off = d_off[3];
+    return rc;
+}
+
 static int run_validate(polylla_ctx *c, cudaStream_t s) {
     CK(cudaMemsetAsync(c->d_bad, 0, sizeof(int32_t), s));
     launch_validate(c->mesh, c->d_bad, s);
@@ -353,9 +397,10 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
         CK(begin(11));
         launch_batch_unpack(c->bv, c->mesh, s);
         launch_batch_ranges(c->bv, c->w, c->poly_off, s);
+        if (c->serve) launch_batch_meta(c->bv, c->w, c->poly_off, c->local_offsets, c->meta, s);
         CK(end(11));
     }
-    c->launches = kKernels + (c->is_batch ? kBatchKernels : 0);
+    c->launches = kKernels + (c->is_batch ? kBatchKernels : 0) + (c->serve ? 1 : 0);
     CK(cudaGetLastError());
     return POLYLLA_OK;
 }
@@ -553,32 +598,11 @@ int polylla_batch_create(polylla_ctx **out, const polylla_batch *b, const polyll
         return POLYLLA_ERR_CUDA;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    c->is_batch = true;
-    const int32_t V = vo[n], T = to[n], H = ho[n];
-    c->mesh.V = V;
-    c->mesh.T = T;
-    c->mesh.H = H;
-    c->mesh.xy = reinterpret_cast<const double2 *>(b->coords);
+    rc = batch_alloc(c, n, vo[n], to[n], ho[n], b->coords, b->origin, b->twin, b->next, b->prev);
     BatchView &bv = c->bv;
-    bv.n = n;
-    bv.T_tot = T;
-    bv.H_tot = H;
-    bv.origin = b->origin;
-    bv.twin = b->twin;
-    bv.next = b->next;
-    bv.prev = b->prev;
-    void *p = nullptr;
-    int32_t *d_off[4] = {nullptr, nullptr, nullptr, nullptr};
-    for (int k = 0; k < 4 && !rc; k++)
-        if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(n + 1))) == 0) d_off[k] = (int32_t *)p;
-    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(n + 1))) == 0) c->poly_off = (int32_t *)p;
-    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_origin = (int32_t *)p;
-    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_twin = (int32_t *)p;
-    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.next = (int32_t *)p;
-    if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.prev = (int32_t *)p;
+    int32_t *d_off[4] = {const_cast<int32_t *>(bv.v_off), const_cast<int32_t *>(bv.t_off),
+                         const_cast<int32_t *>(bv.h_off), const_cast<int32_t *>(bv.b_off)};
     if (!rc) {
-        c->mesh.origin = c->u_origin;
-        c->mesh.twin = c->u_twin;
         // border prefix sums b_off[i] = h_off[i] - 3 t_off[i]
         int32_t *h_b = new (std::nothrow) int32_t[(size_t)n + 1];
         if (!h_b) rc = POLYLLA_ERR_OUT_OF_MEMORY;
@@ -592,13 +616,7 @@ int polylla_batch_create(polylla_ctx **out, const polylla_batch *b, const polyll
             if (e != cudaSuccess) rc = cuda_fail(c, e);
         }
     }
-    if (!rc) {
-        bv.v_off = d_off[0];
-        bv.t_off = d_off[1];
-        bv.h_off = d_off[2];
-        bv.b_off = d_off[3];
-        rc = alloc_work(c, opt);
-    }
+    if (!rc) rc = alloc_work(c, opt);
     if (!rc) {
         c->w.loc_t_off = bv.t_off;
         c->w.loc_v_off = bv.v_off;
@@ -730,3 +748,75 @@ int polylla_tuning_cache_clear(void) {
 }
 
 }  // extern "C"
+
+// ---- serving slots (see polylla_serve.cuh) --------------------------------------
+
+namespace polylla {
+
+int serve_reserve(polylla_ctx **out, int32_t n_cap, int32_t V_cap, int32_t T_cap, int32_t H_cap,
+                  const double *coords, const int32_t *origin, const int32_t *twin, int32_t *next, int32_t *prev,
+                  int32_t max_rotation) {
+    if (!out || n_cap < 1) return POLYLLA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    int rc = check_sizes(V_cap, T_cap, H_cap);
+    if (rc) return rc;
+    polylla_ctx *c = new (std::nothrow) polylla_ctx();
+    if (!c) return POLYLLA_ERR_OUT_OF_MEMORY;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return POLYLLA_ERR_CUDA;
+    }
+    c->serve = true;
+    rc = batch_alloc(c, n_cap, V_cap, T_cap, H_cap, coords, origin, twin, next, prev);
+    void *p = nullptr;
+    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t) * 4 * (size_t)n_cap)) == 0) c->meta = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t) * ((size_t)T_cap + n_cap + 1))) == 0)
+        c->local_offsets = (int32_t *)p;
+    polylla_options opt{0, max_rotation};
+    if (!rc) rc = alloc_work(c, &opt);
+    if (rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    c->w.loc_t_off = c->bv.t_off;
+    c->w.loc_v_off = c->bv.v_off;
+    *out = c;
+    return POLYLLA_OK;
+}
+
+size_t serve_bytes(const polylla_ctx *c) { return c ? c->bytes : 0; }
+
+int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const int32_t *h_off4, cudaStream_t s) {
+    if (!c || !c->serve || n < 1) return POLYLLA_ERR_INVALID_ARGUMENT;
+    c->mesh.V = V;
+    c->mesh.T = T;
+    c->mesh.H = H;
+    c->bv.n = n;
+    c->bv.T_tot = T;
+    c->bv.H_tot = H;
+    c->w.loc_n = n;
+    c->w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
+    c->w.n_chunk_max = (int32_t)((3 * (int64_t)T + CHUNK - 1) / CHUNK);
+    int32_t *dst[4] = {const_cast<int32_t *>(c->bv.v_off), const_cast<int32_t *>(c->bv.t_off),
+                       const_cast<int32_t *>(c->bv.h_off), const_cast<int32_t *>(c->bv.b_off)};
+    for (int k = 0; k < 4; k++)
+        CK(cudaMemcpyAsync(dst[k], h_off4 + (size_t)k * (n + 1), sizeof(int32_t) * (size_t)(n + 1),
+                           cudaMemcpyHostToDevice, s));
+    c->last_stream = s;
+    c->timed_last = false;
+    return enqueue(c, s, false);
+}
+
+void serve_outputs(const polylla_ctx *c, ServeOutputs *o) {
+    o->seeds = c->w.seeds;
+    o->local_offsets = c->local_offsets;
+    o->he_list = c->w.he_list;
+    o->v_list = c->w.v_list;
+    o->meta = c->meta;
+    o->ctrl = c->w.ctrl;
+}
+
+int serve_status(const DevCtrl &h) { return device_status(h); }
+
+}  // namespace polylla

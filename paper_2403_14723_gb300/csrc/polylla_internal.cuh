@@ -208,5 +208,7 @@ void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, i
                        int32_t *bad, cudaStream_t s);
 void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s);
 void launch_batch_ranges(const BatchView &b, const Work &w, int32_t *poly_off, cudaStream_t s);  // two kernels
+void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_off, int32_t *local_offsets,
+                       int32_t *meta, cudaStream_t s);
 
 }  // namespace polylla

@@ -1,0 +1,41 @@
+// Internal interface between the serving runtime (polylla_server.cu) and
+// the context code (polylla_api.cu): a batch context with fixed capacities
+// whose meshes change on every run.
+#pragma once
+
+#include "../../include/polylla.h"
+#include "polylla_internal.cuh"
+
+namespace polylla {
+
+// A batch context able to hold up to n_cap meshes of V_cap, T_cap, H_cap in
+// total, over the caller's device arena (concatenated local arrays of those
+// capacities).  No mesh is bound yet.
+int serve_reserve(polylla_ctx **out, int32_t n_cap, int32_t V_cap, int32_t T_cap, int32_t H_cap,
+                  const double *coords, const int32_t *origin, const int32_t *twin, int32_t *next, int32_t *prev,
+                  int32_t max_rotation);
+
+// Device bytes the context holds.
+size_t serve_bytes(const polylla_ctx *c);
+
+// Bind n meshes of V, T, H in total and enqueue the whole run on s: copies
+// of the prefix sums h_off4 = {v[n+1], t[n+1], h[n+1], b[n+1]} (pinned host
+// memory that must stay valid until they complete), packing, the method's
+// stages, unpacking and the per-mesh metadata.
+int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const int32_t *h_off4, cudaStream_t s);
+
+// Device outputs of the last run (valid once it completes, until the next).
+struct ServeOutputs {
+    const int32_t *seeds;          // batch order, mesh-local values
+    const int32_t *local_offsets;  // mesh i: [first polygon + i, ... + P_i + 1)
+    const int32_t *he_list;        // mesh-local values
+    const int32_t *v_list;
+    const int32_t *meta;           // [4 n]: P_i, N_F,i, first polygon, first CSR entry
+    const DevCtrl *ctrl;
+};
+void serve_outputs(const polylla_ctx *c, ServeOutputs *o);
+
+// Status a run's control block reports (POLYLLA_OK or a device error).
+int serve_status(const DevCtrl &h);
+
+}  // namespace polylla

@@ -1,0 +1,481 @@
+// Serving runtime (no counterpart in the paper): a request loop with
+// continuous batching over the batched generate.
+//
+// One scheduler thread owns every CUDA call.  Requests wait in a FIFO queue
+// in host memory; whenever a slot is free the scheduler takes, in arrival
+// order, as many waiting requests as fit the slot's capacity (meshes,
+// triangles, vertices, half-edges), copies their host arrays into the
+// slot's device arena, runs the batch (pack, the method's stages, unpack,
+// per-mesh metadata) and copies the per-mesh metadata back.  When that has
+// landed it copies each request's CSR slices and next/prev back into the
+// request's host buffers; when those land the requests complete.  Each
+// slot has its own stream, so one slot's copies overlap another's kernels.
+// Slots and arenas are allocated once, at create, within the memory budget:
+// admission against device memory is admission into a slot.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "polylla_serve.cuh"
+
+using namespace polylla;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr int kMaxSlots = 16;
+
+struct Req {
+    polylla_request r{};
+    int64_t ticket = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int status = POLYLLA_OK;
+    int32_t P = 0, NF = 0, batch_meshes = 0;
+    bool done = false;
+};
+
+struct Slot {
+    polylla_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_meta = nullptr, ev_out = nullptr;
+    double *coords = nullptr;  // device arena: concatenated local arrays
+    int32_t *origin = nullptr, *twin = nullptr, *next = nullptr, *prev = nullptr;
+    int32_t *h_off = nullptr;  // pinned [4 (n_cap + 1)]: v, t, h, b prefix sums
+    int32_t *h_meta = nullptr; // pinned [4 n_cap]
+    DevCtrl *h_ctrl = nullptr; // pinned
+    int32_t n_cap = 0, V_cap = 0, T_cap = 0, H_cap = 0;
+    std::vector<Req *> reqs;
+    int state = 0;             // 0 free, 1 batch running, 2 copying results out
+};
+
+// Device bytes of one slot of triangle capacity T (arena, union, scratch,
+// metadata), following the allocations of serve_reserve and the arena.
+int64_t slot_bytes(int64_t n, int64_t V, int64_t T, int64_t H) {
+    const int64_t arena = 16 * V + 16 * H;
+    const int64_t uni = 16 * H + 20 * (n + 1);
+    const int64_t meta = 16 * n + 4 * (T + n + 1);
+    const int64_t Tpad = (T + 15) / 16 * 16;
+    const int64_t work = 2 * Tpad + 8 * V + 16 * ((T + CC_TRI - 1) / CC_TRI) + 16 * ((3 * T + CHUNK - 1) / CHUNK) +
+                         8 * ((3 * T + 31) / 32) + 24 * T + 4 * T + 4 * (T + 1) + 24 * T + 256;
+    return arena + uni + meta + work + 64 * 256;  // + allocation rounding
+}
+
+}  // namespace
+
+struct polylla_server {
+    int device = 0;
+    int32_t max_batch = 4096;
+    int32_t max_rotation = 0;
+    int n_slots = 0;
+    Slot slots[kMaxSlots];
+    int64_t device_bytes = 0;
+    Clock::time_point t0;
+
+    std::mutex mu;
+    std::condition_variable cv_submit, cv_done;
+    std::deque<Req *> pending;
+    std::unordered_map<int64_t, Req *> reqs;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    std::thread sched;
+
+    int64_t batches = 0, done_count = 0;
+    double busy = 0.0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+    void loop();
+    bool launch(Slot &s);
+    void copy_out(Slot &s);
+    void finish(Slot &s, int status);
+    void complete(Req *q, int status);
+};
+
+void polylla_server::complete(Req *q, int status) {
+    std::lock_guard<std::mutex> g(mu);
+    q->status = status;
+    q->t_done = now();
+    q->done = true;
+    done_count++;
+    cv_done.notify_all();
+}
+
+void polylla_server::finish(Slot &s, int status) {
+    for (Req *q : s.reqs) complete(q, status);
+    s.reqs.clear();
+    s.state = 0;
+}
+
+// Form a batch from the head of the queue and enqueue it on the slot.
+// Returns true when a batch was launched.
+bool polylla_server::launch(Slot &s) {
+    std::vector<Req *> take;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        int64_t V = 0, T = 0, H = 0;
+        while (!pending.empty() && (int32_t)take.size() < std::min(s.n_cap, max_batch)) {
+            Req *q = pending.front();
+            const polylla_request &r = q->r;
+            if (r.n_vertices > s.V_cap || r.n_triangles > s.T_cap || r.n_halfedges > s.H_cap) {
+                // larger than any slot: fails now (slots are identical)
+                pending.pop_front();
+                q->status = POLYLLA_ERR_TOO_LARGE;
+                q->t_admit = q->t_done = now();
+                q->done = true;
+                done_count++;
+                cv_done.notify_all();
+                continue;
+            }
+            if (V + r.n_vertices > s.V_cap || T + r.n_triangles > s.T_cap || H + r.n_halfedges > s.H_cap) break;
+            V += r.n_vertices;
+            T += r.n_triangles;
+            H += r.n_halfedges;
+            take.push_back(q);
+            pending.pop_front();
+        }
+    }
+    if (take.empty()) return false;
+    const int32_t n = (int32_t)take.size();
+    int32_t *vo = s.h_off, *to = vo + (n + 1), *ho = to + (n + 1), *bo = ho + (n + 1);
+    vo[0] = to[0] = ho[0] = bo[0] = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const polylla_request &r = take[i]->r;
+        vo[i + 1] = vo[i] + r.n_vertices;
+        to[i + 1] = to[i] + r.n_triangles;
+        ho[i + 1] = ho[i] + r.n_halfedges;
+        bo[i + 1] = ho[i + 1] - 3 * to[i + 1];
+    }
+    const double t = now();
+    s.reqs = take;
+    for (Req *q : take) {
+        q->t_admit = t;
+        q->batch_meshes = n;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
+        const polylla_request &r = take[i]->r;
+        const size_t Hb = 4 * (size_t)r.n_halfedges;
+        e = cudaMemcpyAsync(s.coords + 2 * (size_t)vo[i], r.mesh.coords, 16 * (size_t)r.n_vertices,
+                            cudaMemcpyHostToDevice, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.origin + ho[i], r.mesh.origin, Hb, cudaMemcpyHostToDevice, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.twin + ho[i], r.mesh.twin, Hb, cudaMemcpyHostToDevice, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.next + ho[i], r.mesh.next, Hb, cudaMemcpyHostToDevice, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.prev + ho[i], r.mesh.prev, Hb, cudaMemcpyHostToDevice, s.stream);
+    }
+    int rc = e == cudaSuccess ? serve_run(s.ctx, n, vo[n], to[n], ho[n], s.h_off, s.stream) : POLYLLA_ERR_CUDA;
+    if (rc == POLYLLA_OK) {
+        ServeOutputs o;
+        serve_outputs(s.ctx, &o);
+        e = cudaMemcpyAsync(s.h_meta, o.meta, 16 * (size_t)n, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_ctrl, o.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(s.ev_meta, s.stream);
+        if (e != cudaSuccess) rc = POLYLLA_ERR_CUDA;
+    }
+    if (rc != POLYLLA_OK) {
+        cudaStreamSynchronize(s.stream);
+        finish(s, rc);
+        return true;
+    }
+    s.state = 1;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        batches++;
+    }
+    return true;
+}
+
+// The batch's metadata has landed: copy every request's results out.
+void polylla_server::copy_out(Slot &s) {
+    const int status = serve_status(*s.h_ctrl);
+    if (status != POLYLLA_OK) {
+        finish(s, status);
+        return;
+    }
+    ServeOutputs o;
+    serve_outputs(s.ctx, &o);
+    const int32_t n = (int32_t)s.reqs.size();
+    const int32_t *ho = s.h_off + 2 * (n + 1);
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
+        Req *q = s.reqs[i];
+        polylla_host_result &out = q->r.result;
+        const int32_t P = s.h_meta[4 * i], NF = s.h_meta[4 * i + 1];
+        const int32_t p0 = s.h_meta[4 * i + 2], c0 = s.h_meta[4 * i + 3];
+        q->P = P;
+        q->NF = NF;
+        const size_t Hb = 4 * (size_t)q->r.n_halfedges;
+        e = cudaMemcpyAsync(out.seeds, o.seeds + p0, 4 * (size_t)P, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out.offsets, o.local_offsets + p0 + i, 4 * (size_t)(P + 1), cudaMemcpyDeviceToHost,
+                                s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.he_list, o.he_list + c0, 4 * (size_t)NF, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.v_list, o.v_list + c0, 4 * (size_t)NF, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.next, s.next + ho[i], Hb, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.prev, s.prev + ho[i], Hb, cudaMemcpyDeviceToHost, s.stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev_out, s.stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s.stream);
+        finish(s, POLYLLA_ERR_CUDA);
+        return;
+    }
+    s.state = 2;
+}
+
+void polylla_server::loop() {
+    cudaSetDevice(device);
+    double busy_since = -1.0;
+    for (;;) {
+        bool progressed = false;
+        int in_flight = 0;
+        for (int k = 0; k < n_slots; k++) {
+            Slot &s = slots[k];
+            if (s.state == 1) {
+                const cudaError_t q = cudaEventQuery(s.ev_meta);
+                if (q == cudaSuccess) {
+                    copy_out(s);
+                    progressed = true;
+                } else if (q != cudaErrorNotReady) {
+                    finish(s, POLYLLA_ERR_CUDA);
+                    progressed = true;
+                }
+            }
+            if (s.state == 2) {
+                const cudaError_t q = cudaEventQuery(s.ev_out);
+                if (q == cudaSuccess || q != cudaErrorNotReady) {
+                    for (Req *r : s.reqs) {
+                        r->r.result.n_polygons = r->P;
+                        r->r.result.n_frontier = r->NF;
+                    }
+                    finish(s, q == cudaSuccess ? POLYLLA_OK : POLYLLA_ERR_CUDA);
+                    progressed = true;
+                }
+            }
+        }
+        for (int k = 0; k < n_slots; k++)
+            if (slots[k].state == 0 && launch(slots[k])) progressed = true;
+        for (int k = 0; k < n_slots; k++) in_flight += slots[k].state != 0;
+        const double t = now();
+        if (in_flight && busy_since < 0) busy_since = t;
+        if (!in_flight && busy_since >= 0) {
+            std::lock_guard<std::mutex> g(mu);
+            busy += t - busy_since;
+            busy_since = -1.0;
+        }
+        if (progressed) continue;
+        std::unique_lock<std::mutex> g(mu);
+        if (stop && pending.empty() && !in_flight) break;
+        if (in_flight) {
+            // batches on the GPU: poll their events again shortly
+            g.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        } else {
+            cv_submit.wait_for(g, std::chrono::milliseconds(5), [&] { return stop || !pending.empty(); });
+        }
+    }
+    if (busy_since >= 0) {
+        std::lock_guard<std::mutex> g(mu);
+        busy += now() - busy_since;
+    }
+}
+
+static void free_slot(Slot &s) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.ctx) polylla_destroy(s.ctx);
+    if (s.coords) cudaFree(s.coords);
+    if (s.origin) cudaFree(s.origin);
+    if (s.twin) cudaFree(s.twin);
+    if (s.next) cudaFree(s.next);
+    if (s.prev) cudaFree(s.prev);
+    if (s.h_off) cudaFreeHost(s.h_off);
+    if (s.h_meta) cudaFreeHost(s.h_meta);
+    if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
+    if (s.ev_meta) cudaEventDestroy(s.ev_meta);
+    if (s.ev_out) cudaEventDestroy(s.ev_out);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = Slot();
+}
+
+static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t T, int32_t H) {
+    s.n_cap = n;
+    s.V_cap = V;
+    s.T_cap = T;
+    s.H_cap = H;
+    cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_meta, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.coords, 16 * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.origin, 4 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.twin, 4 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.next, 4 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.prev, 4 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_off, sizeof(int32_t) * 4 * ((size_t)n + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_meta, sizeof(int32_t) * 4 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_ctrl, sizeof(DevCtrl));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? POLYLLA_ERR_OUT_OF_MEMORY : POLYLLA_ERR_CUDA;
+    const int rc = serve_reserve(&s.ctx, n, V, T, H, s.coords, s.origin, s.twin, s.next, s.prev, srv->max_rotation);
+    if (rc) return rc;
+    srv->device_bytes += 16 * (int64_t)V + 16 * (int64_t)H + (int64_t)serve_bytes(s.ctx);
+    return POLYLLA_OK;
+}
+
+extern "C" {
+
+int polylla_server_create(polylla_server **out, const polylla_server_options *opt) {
+    if (!out) return POLYLLA_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (!opt || opt->memory_budget <= 0 || opt->n_slots < 0 || opt->n_slots > kMaxSlots || opt->max_batch_meshes < 0 ||
+        opt->max_rotation < 0)
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    polylla_server *srv = new (std::nothrow) polylla_server();
+    if (!srv) return POLYLLA_ERR_OUT_OF_MEMORY;
+    if (cudaGetDevice(&srv->device) != cudaSuccess) {
+        delete srv;
+        return POLYLLA_ERR_CUDA;
+    }
+    srv->n_slots = opt->n_slots ? opt->n_slots : 3;
+    srv->max_batch = opt->max_batch_meshes ? opt->max_batch_meshes : 4096;
+    srv->max_rotation = opt->max_rotation;
+    // slot capacity: the largest T whose slot, with V <= T + 2n and
+    // H <= 4T + 2n (bounds for triangulated disks), fits budget / n_slots
+    const int64_t per = opt->memory_budget / srv->n_slots;
+    const int64_t n = srv->max_batch;
+    int64_t lo = 0, hi = 500000000;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (slot_bytes(n, mid + 2 * n, mid, 4 * mid + 2 * n) <= per) lo = mid;
+        else hi = mid - 1;
+    }
+    if (lo < 1) {
+        delete srv;
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    }
+    const int32_t T = (int32_t)lo, V = (int32_t)(lo + 2 * n), H = (int32_t)(4 * lo + 2 * n);
+    int rc = POLYLLA_OK;
+    for (int k = 0; k < srv->n_slots && !rc; k++) rc = make_slot(srv, srv->slots[k], (int32_t)n, V, T, H);
+    if (rc) {
+        for (int k = 0; k < srv->n_slots; k++) free_slot(srv->slots[k]);
+        delete srv;
+        return rc;
+    }
+    srv->t0 = Clock::now();
+    srv->sched = std::thread([srv] { srv->loop(); });
+    *out = srv;
+    return POLYLLA_OK;
+}
+
+int polylla_server_submit(polylla_server *srv, const polylla_request *req, int64_t *ticket) {
+    if (!srv || !req || !ticket) return POLYLLA_ERR_INVALID_ARGUMENT;
+    const polylla_request &r = *req;
+    if (r.n_vertices < 3 || r.n_triangles < 1 || (int64_t)r.n_halfedges < 3 * (int64_t)r.n_triangles + 3)
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    if (!r.mesh.coords || !r.mesh.origin || !r.mesh.twin || !r.mesh.next || !r.mesh.prev || !r.result.seeds ||
+        !r.result.offsets || !r.result.he_list || !r.result.v_list || !r.result.next || !r.result.prev)
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    Req *q = new (std::nothrow) Req();
+    if (!q) return POLYLLA_ERR_OUT_OF_MEMORY;
+    q->r = r;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        q->ticket = srv->next_ticket++;
+        q->t_submit = srv->now();
+        srv->reqs[q->ticket] = q;
+        srv->pending.push_back(q);
+    }
+    srv->cv_submit.notify_one();
+    *ticket = q->ticket;
+    return POLYLLA_OK;
+}
+
+int polylla_server_wait(polylla_server *srv, int64_t ticket, polylla_request_info *info) {
+    if (!srv) return POLYLLA_ERR_INVALID_ARGUMENT;
+    std::unique_lock<std::mutex> g(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return POLYLLA_ERR_INVALID_ARGUMENT;
+    Req *q = it->second;
+    srv->cv_done.wait(g, [&] { return q->done; });
+    srv->reqs.erase(it);
+    g.unlock();
+    if (info) {
+        info->status = q->status;
+        info->n_polygons = q->P;
+        info->n_frontier = q->NF;
+        info->batch_meshes = q->batch_meshes;
+        info->t_submit = q->t_submit;
+        info->t_admit = q->t_admit;
+        info->t_done = q->t_done;
+    }
+    const int st = q->status;
+    delete q;
+    return st;
+}
+
+int polylla_server_replay(polylla_server *srv, int32_t n, const polylla_request *reqs, const double *arrival_s,
+                          double *latency_s, polylla_request_info *infos) {
+    if (!srv || n < 0 || (n > 0 && (!reqs || !arrival_s || !latency_s))) return POLYLLA_ERR_INVALID_ARGUMENT;
+    std::vector<int64_t> tickets((size_t)n);
+    std::vector<double> sched((size_t)n);
+    const double start = srv->now();
+    int first_err = POLYLLA_OK;
+    for (int32_t k = 0; k < n; k++) {
+        const double at = start + arrival_s[k];
+        sched[k] = at;
+        // sleep to within 200 us of the arrival, then spin
+        for (;;) {
+            const double left = at - srv->now();
+            if (left <= 0) break;
+            if (left > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(left - 1.5e-4));
+        }
+        const int rc = polylla_server_submit(srv, &reqs[k], &tickets[k]);
+        if (rc) {
+            tickets[k] = 0;
+            if (!first_err) first_err = rc;
+            latency_s[k] = -1.0;
+        }
+    }
+    for (int32_t k = 0; k < n; k++) {
+        if (!tickets[k]) continue;
+        polylla_request_info info;
+        const int rc = polylla_server_wait(srv, tickets[k], &info);
+        if (rc && !first_err) first_err = rc;
+        latency_s[k] = info.t_done - sched[k];
+        info.t_submit = sched[k];
+        if (infos) infos[k] = info;
+    }
+    return first_err;
+}
+
+int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out) {
+    if (!srv || !out) return POLYLLA_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> g(srv->mu);
+    out->n_slots = srv->n_slots;
+    out->slot_triangles = srv->slots[0].T_cap;
+    out->device_bytes = srv->device_bytes;
+    out->batches = srv->batches;
+    out->requests_done = srv->done_count;
+    out->busy_seconds = srv->busy;
+    return POLYLLA_OK;
+}
+
+void polylla_server_destroy(polylla_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_submit.notify_all();
+    if (srv->sched.joinable()) srv->sched.join();
+    for (int k = 0; k < srv->n_slots; k++) free_slot(srv->slots[k]);
+    for (auto &kv : srv->reqs) delete kv.second;
+    delete srv;
+}
+
+}  // extern "C"

@@ -84,6 +84,27 @@ class polylla_tuning(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class polylla_server_options(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("n_slots", ctypes.c_int32),
+                ("max_batch_meshes", ctypes.c_int32), ("max_rotation", ctypes.c_int32)]
+
+
+class polylla_request(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32), ("n_halfedges", ctypes.c_int32),
+                ("mesh", polylla_host_mesh), ("result", polylla_host_result)]
+
+
+class polylla_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_polygons", ctypes.c_int32), ("n_frontier", ctypes.c_int32),
+                ("batch_meshes", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class polylla_server_stats(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("slot_triangles", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("requests_done", ctypes.c_int64), ("busy_seconds", ctypes.c_double)]
+
+
 # every function the header declares, with its ctypes signature
 _SIGNATURES = {
     "polylla_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_mesh),
@@ -117,6 +138,15 @@ _SIGNATURES = {
     "polylla_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(polylla_tuning),
                                         ctypes.c_void_p]),
     "polylla_tuning_cache_clear": (ctypes.c_int, []),
+    "polylla_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_server_options)]),
+    "polylla_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_request),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "polylla_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(polylla_request_info)]),
+    "polylla_server_replay": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(polylla_request),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(polylla_request_info)]),
+    "polylla_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_server_stats)]),
+    "polylla_server_destroy": (None, [ctypes.c_void_p]),
 }
 
 _lib = None
@@ -448,6 +478,96 @@ def polylla_batch_polygon_offsets(ctx: int, n_meshes: int):
     _check(load_library().polylla_batch_polygon_offsets(ctypes.c_void_p(ctx), ctypes.byref(p)),
            "polylla_batch_polygon_offsets")
     return _view(p.value, n_meshes + 1, "<i4", torch.int32)
+
+
+class HostRequest:
+    """A mesh in pinned host memory plus pinned result buffers of the
+    capacities a request needs (T, T+1, 3T, 3T, H, H)."""
+
+    def __init__(self, mesh):
+        import torch
+
+        self.mesh = mesh
+        T, H = int(mesh.n_triangles), int(mesh.n_halfedges)
+        self.inp = {k: torch.from_numpy(getattr(mesh, k)).contiguous().pin_memory()
+                    for k in ("coords", "origin", "twin", "next", "prev")}
+        self.out = {"seeds": torch.empty(T, dtype=torch.int32).pin_memory(),
+                    "offsets": torch.empty(T + 1, dtype=torch.int32).pin_memory(),
+                    "he_list": torch.empty(3 * T, dtype=torch.int32).pin_memory(),
+                    "v_list": torch.empty(3 * T, dtype=torch.int32).pin_memory(),
+                    "next": torch.empty(H, dtype=torch.int32).pin_memory(),
+                    "prev": torch.empty(H, dtype=torch.int32).pin_memory()}
+        self.req = polylla_request(
+            int(mesh.n_vertices), T, H,
+            polylla_host_mesh(*(ctypes.c_void_p(self.inp[k].data_ptr())
+                                for k in ("coords", "origin", "twin", "next", "prev"))),
+            polylla_host_result(*(ctypes.c_void_p(self.out[k].data_ptr())
+                                  for k in ("seeds", "offsets", "he_list", "v_list", "next", "prev")), 0, 0))
+
+    def result(self, info: dict) -> dict:
+        """Numpy copies of the outputs, trimmed to the request's P and N_F."""
+        P, NF = info["n_polygons"], info["n_frontier"]
+        return {"seeds": self.out["seeds"][:P].numpy().copy(), "offsets": self.out["offsets"][:P + 1].numpy().copy(),
+                "he_list": self.out["he_list"][:NF].numpy().copy(), "v_list": self.out["v_list"][:NF].numpy().copy(),
+                "next": self.out["next"].numpy().copy(), "prev": self.out["prev"].numpy().copy()}
+
+
+def _info_dict(info: polylla_request_info) -> dict:
+    return {k: getattr(info, k) for k, _ in polylla_request_info._fields_}
+
+
+class Server:
+    """The serving loop (``polylla_server_*``): continuous batching of host
+    requests on the current device."""
+
+    def __init__(self, memory_budget: int, n_slots: int = 3, max_batch_meshes: int = 0, max_rotation: int = 0):
+        lib = load_library()
+        opt = polylla_server_options(int(memory_budget), int(n_slots), int(max_batch_meshes), int(max_rotation))
+        h = ctypes.c_void_p()
+        _check(lib.polylla_server_create(ctypes.byref(h), ctypes.byref(opt)), "polylla_server_create")
+        self.h = h.value
+
+    def submit(self, r: HostRequest) -> int:
+        t = ctypes.c_int64()
+        _check(load_library().polylla_server_submit(ctypes.c_void_p(self.h), ctypes.byref(r.req), ctypes.byref(t)),
+               "polylla_server_submit")
+        return t.value
+
+    def wait(self, ticket: int) -> dict:
+        info = polylla_request_info()
+        load_library().polylla_server_wait(ctypes.c_void_p(self.h), int(ticket), ctypes.byref(info))
+        return _info_dict(info)
+
+    def replay(self, requests, arrival_s) -> tuple:
+        """Open-loop replay (native): returns (status, latencies [s], infos)."""
+        import numpy as np
+
+        n = len(requests)
+        arr = (polylla_request * n)(*[r.req for r in requests])
+        at = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(n, dtype=np.float64)
+        infos = (polylla_request_info * n)()
+        rc = load_library().polylla_server_replay(
+            ctypes.c_void_p(self.h), n, arr, at.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), infos)
+        return rc, lat, [_info_dict(i) for i in infos]
+
+    def stats(self) -> dict:
+        st = polylla_server_stats()
+        _check(load_library().polylla_server_get_stats(ctypes.c_void_p(self.h), ctypes.byref(st)),
+               "polylla_server_get_stats")
+        return {k: getattr(st, k) for k, _ in polylla_server_stats._fields_}
+
+    def close(self):
+        if self.h:
+            load_library().polylla_server_destroy(ctypes.c_void_p(self.h))
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Polylla:

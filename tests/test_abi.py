@@ -75,6 +75,16 @@ def test_null_arguments_rejected_without_gpu(lib_path):
     assert lib.polylla_set_tuning(None, None) == -1
     assert lib.polylla_batch_polygon_offsets(None, None) == -1
     assert lib.polylla_tuning_cache_clear() == 0
+    srv = ctypes.c_void_p()
+    assert lib.polylla_server_create(None, None) == -1
+    assert lib.polylla_server_create(ctypes.byref(srv), None) == -1
+    bad = polylla.polylla_server_options(0, 3, 0, 0)                     # no memory budget
+    assert lib.polylla_server_create(ctypes.byref(srv), ctypes.byref(bad)) == -1
+    bad = polylla.polylla_server_options(1 << 30, 99, 0, 0)              # too many slots
+    assert lib.polylla_server_create(ctypes.byref(srv), ctypes.byref(bad)) == -1
+    assert lib.polylla_server_submit(None, None, None) == -1
+    assert lib.polylla_server_get_stats(None, None) == -1
+    assert lib.polylla_server_replay(None, 0, None, None, None, None) == -1
 
 
 def test_built_for_sm_103a_only():

@@ -1,0 +1,91 @@
+"""The serving loop through the C ABI: requests batched continuously must
+each get exactly the oracle's result for their mesh alone (bit-exact), the
+same whether a request ran alone or in a mix, and a request too large for a
+slot must fail cleanly."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2403_14723_gb300 import build, meshgen, polylla
+
+pytestmark = pytest.mark.gpu
+
+
+def _meshes():
+    ms = [meshgen.two_triangle_square(), meshgen.exact_grid(6), meshgen.perturbed_grid(40, 0.3, seed=21)]
+    for s in range(60):                        # meshes with barrier tips
+        m = meshgen.random_delaunay(150, seed=7000 + s)
+        if oracle.run_mesh(m).stats["tips"] >= 1:
+            ms.append(m)
+        if len(ms) >= 6:
+            break
+    ms += meshgen.random_batch(24, t_min=1000, t_max=50_000, seed=50)
+    ms.append(meshgen.perturbed_grid(400, 0.3, seed=22))      # ~318k triangles
+    return ms
+
+
+def _check(mesh, info, res, r, tag):
+    assert info["status"] == 0, tag
+    assert info["n_polygons"] == r.n_polygons and info["n_frontier"] == r.he_list.shape[0], tag
+    for k, want in (("seeds", r.seeds), ("offsets", r.offsets), ("he_list", r.he_list), ("v_list", r.v_list),
+                    ("next", r.next_out), ("prev", r.prev_out)):
+        assert np.array_equal(res[k], want), f"{tag}: {k} differs"
+
+
+def test_served_requests_match_oracle_alone_and_in_the_mix():
+    build.build_library()
+    meshes = _meshes()
+    oracle_res = [oracle.run_mesh(m) for m in meshes]
+    with polylla.Server(memory_budget=3 << 30, n_slots=3, max_batch_meshes=16) as srv:
+        # alone: one request at a time
+        alone = []
+        for i in (0, 4, len(meshes) - 1):
+            hr = polylla.HostRequest(meshes[i])
+            info = srv.wait(srv.submit(hr))
+            assert info["batch_meshes"] == 1
+            alone.append((i, hr.result(info)))
+            _check(meshes[i], info, alone[-1][1], oracle_res[i], f"alone {meshes[i].name}")
+        # in the mix: everything at once, so batches form and overlap
+        reqs = [polylla.HostRequest(m) for m in meshes]
+        tickets = [srv.submit(r) for r in reqs]
+        infos = [srv.wait(t) for t in tickets]
+        assert max(i["batch_meshes"] for i in infos) > 1, "no request was batched with another"
+        for m, hr, info, r in zip(meshes, reqs, infos, oracle_res):
+            _check(m, info, hr.result(info), r, f"mix {m.name}")
+        for i, res in alone:
+            mixed = reqs[i].result(infos[i])
+            for k in res:
+                assert np.array_equal(res[k], mixed[k]), f"{meshes[i].name}: {k} differs alone vs in the mix"
+        st = srv.stats()
+        assert st["requests_done"] == len(meshes) + 3 and st["batches"] >= 4
+        assert st["device_bytes"] <= 3 << 30
+
+
+def test_replay_poisson_trace():
+    build.build_library()
+    pool = meshgen.random_batch(16, t_min=1000, t_max=50_000, seed=51)
+    hrs = [polylla.HostRequest(m) for m in pool]
+    rng = np.random.default_rng(5)
+    n = 400
+    arrival = np.cumsum(rng.exponential(1 / 2000.0, size=n))
+    pick = rng.integers(0, len(pool), size=n)
+    with polylla.Server(memory_budget=2 << 30, n_slots=3) as srv:
+        rc, lat, infos = srv.replay([hrs[i] for i in pick], arrival)
+    assert rc == 0
+    assert np.all(lat > 0) and np.all(np.isfinite(lat))
+    r0 = oracle.run_mesh(pool[int(pick[-1])])
+    assert infos[-1]["n_polygons"] == r0.n_polygons
+
+
+def test_request_larger_than_a_slot_fails_cleanly():
+    build.build_library()
+    with polylla.Server(memory_budget=64 << 20, n_slots=2, max_batch_meshes=4) as srv:
+        cap = srv.stats()["slot_triangles"]
+        big = meshgen.perturbed_grid(int(np.sqrt(cap)) + 10, 0.3, seed=2)
+        assert big.n_triangles > cap
+        info = srv.wait(srv.submit(polylla.HostRequest(big)))
+        assert info["status"] == -8
+        small = meshgen.exact_grid(5)
+        hr = polylla.HostRequest(small)
+        info = srv.wait(srv.submit(hr))
+        _check(small, info, hr.result(info), oracle.run_mesh(small), "after a rejected request")
