@@ -37,7 +37,10 @@ def _digest(extra=()) -> str:
     for f in [os.path.join(CSRC, s) for s in SOURCES] + HEADERS:
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra)).encode())
+    # the include directory is an absolute path that differs between
+    # checkouts; leave it out so a source digest is the same everywhere
+    flags = [f for f in NVCC_FLAGS if not f.startswith("-I")]
+    h.update(" ".join(ARCH + flags + list(extra)).encode())
     return h.hexdigest()[:12]
 
 
