@@ -509,7 +509,7 @@ def run_batched(args):
             ms = timed(args.steps, step)
         dist_barrier(ws)
         ms = dist_max(ms, ws)
-        launches = args.steps * 15
+        launches = args.steps * 14
         out = polylla.polylla_get_polygons(ctx, stream)
         P, NF = out["n_polygons"], out["n_frontier"]
         po = polylla.polylla_batch_polygon_offsets(ctx, n_meshes).cpu().numpy()
@@ -609,7 +609,7 @@ def run_batched(args):
                        "parallelism": f"replicas x{ws}", "cuda_graph": True, "tuning": tuning,
                        "l2": "256 MiB buffer written between timed steps; inputs exceed L2"},
             "one_mesh_at_a_time": {"value": ws * T / (ms_loop * 1e-3), "unit": UNIT, "ms_per_step": ms_loop,
-                                   "launches_per_step": 11 * n_meshes,
+                                   "launches_per_step": 10 * n_meshes,
                                    "how": "polylla_generate per mesh, back to back on one stream"},
             "without_graph": {"value": ws * T / (ms_nograph * 1e-3), "unit": UNIT, "ms_per_step": ms_nograph},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -733,7 +733,7 @@ def run_served(args):
                     "d2h_bytes_per_step": main["d2h_bytes"] // max(1, main["requests"]),
                     "api": "polylla_server_replay: host meshes in, host results out, per request"},
             "roofline": None, "cpu_baseline": None,
-            "gpu_launches": batches * 16, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
+            "gpu_launches": batches * 15, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

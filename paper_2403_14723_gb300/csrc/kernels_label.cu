@@ -293,8 +293,6 @@ __global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
     const int32_t nE = 3 * nT;
     const int32_t HI = 3 * m.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < nE; i += NT) s_pv[i] = -1;
-    __syncthreads();
     const int32_t t = t0 + threadIdx.x;
     const bool live = threadIdx.x < nT;
     const int32_t e0 = 3 * t;
@@ -321,18 +319,23 @@ __global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
         const int32_t twl = lt == 0u ? tw[0] : (lt == 1u ? tw[1] : tw[2]);
         const bool seed = (twl >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < twl);
         fl = F | ((uint32_t)seed << 6);
+        // own slots first: non-frontier half-edges keep their triangle
+        // links, frontier ones wait for their predecessor (-1 until then)
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const int j = k == 2 ? 0 : k + 1;
-            if (!((F >> k) & 1u)) {
-                s_nx[lb + k] = e0 + j;
-                s_pv[lb + k] = e0 + (k == 0 ? 2 : k - 1);
-            } else if ((F >> j) & 1u) {
-                s_nx[lb + k] = e0 + j;   // successor in the same triangle
-                s_pv[lb + j] = e0 + k;
-            } else {
-                pend |= 1u << k;
-            }
+            const bool f = (F >> k) & 1u;
+            s_pv[lb + k] = f ? -1 : e0 + (k == 0 ? 2 : k - 1);
+            if (!f || ((F >> j) & 1u)) s_nx[lb + k] = e0 + j;
+            else pend |= 1u << k;
+        }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int j = k == 2 ? 0 : k + 1;
+            if (((fl >> k) & 1u) && ((fl >> j) & 1u)) s_pv[lb + j] = e0 + k;  // successor in the same triangle
         }
     }
     // compact the warp's pending rotations

@@ -17,9 +17,9 @@
 //   k_scan_blocks exclusive scan of those counts            (one block)
 //   k_cand_write  the walk starts, in index order           (scan-compaction)
 //   k_walk        one chain per lane, grid-stride, two chains interleaved;
-//                 (polygon count, length) per 2048-start chunk by per-warp
-//                 atomics
-//   k_scan_blocks exclusive scan of the chunk totals -> P, N_F
+//                 (polygon count, length) per 32 starts, and per
+//                 2048-start chunk by per-warp atomics
+//   k_scan_blocks exclusive scan of the chunk totals -> P, N_F, offsets[P]
 //   k_emit        per warp and 64 starts: offsets by warp scan over the
 //                 chunk prefix and the group totals before it; every
 //                 minimum writes its seed and offset and lists its polygon
@@ -28,9 +28,6 @@
 #include "polylla_internal.cuh"
 
 namespace polylla {
-
-// bits 0-2 frontier, bits 3-5 walk-start mark: a start is both
-__device__ __forceinline__ uint32_t starts_of(uint32_t f) { return f & (f >> 3) & 7u; }
 
 __device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long v, int lane) {
 #pragma unroll
@@ -47,23 +44,51 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
-// exclusive block scan of one value per thread (blockDim.x <= 1024);
-// returns the exclusive prefix, *total gets the block total
+// exclusive block scan of one value per thread (blockDim.x a multiple of
+// 32, at most 1024); returns the exclusive prefix, *total gets the block
+// total.  s_warp holds 32 + 1 entries.
 __device__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long *s_warp,
                                               unsigned long long *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned long long inc = warp_incl_scan(v, lane);
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    unsigned long long wb = 0, t = 0;
-    for (int q = 0; q < nw; q++) {
-        const unsigned long long x = s_warp[q];
-        if (q < warp) wb += x;
-        t += x;
+    if (warp == 0) {
+        // one warp scans the warp totals: s_warp[q] becomes the exclusive
+        // prefix of warp q, s_warp[32] the block total
+        const unsigned long long x = lane < nw ? s_warp[lane] : 0ull;
+        const unsigned long long xi = warp_incl_scan(x, lane);
+        if (lane < nw) s_warp[lane] = xi - x;
+        if (lane == 31) s_warp[32] = xi;
     }
+    __syncthreads();
+    const unsigned long long wb = s_warp[warp];
+    *total = s_warp[32];
     __syncthreads();  // s_warp may be reused by the caller
-    *total = t;
     return wb + inc - v;
+}
+
+// The walk starts of 16 triangles t0 .. t0+15 as four words: byte q of
+// word i holds the start bits of triangle t0 + 4i + q in its low 3 bits
+// (a start is frontier and marked: f & (f >> 3) & 7 per flags byte, done
+// on four bytes at once; bits shifted in from the next byte are masked).
+// flags is allocated to a multiple of 16 bytes: the int4 stays in bounds.
+__device__ __forceinline__ void start_words(const MeshView &m, const Work &w, int32_t t0, uint32_t st[4]) {
+    st[0] = st[1] = st[2] = st[3] = 0u;
+    if (t0 >= m.T) return;
+    const int4 v = *reinterpret_cast<const int4 *>(w.flags + t0);
+    const uint32_t wd[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) st[i] = wd[i] & (wd[i] >> 3) & 0x07070707u;
+    const int32_t valid = m.T - t0;  // triangles of the 16 inside [0, T)
+    if (valid < 16) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int32_t keep = valid - 4 * i;  // bytes of word i to keep
+            if (keep <= 0) st[i] = 0u;
+            else if (keep < 4) st[i] &= (1u << (8 * keep)) - 1u;
+        }
+    }
 }
 
 // ===========================================================================
@@ -71,19 +96,13 @@ __device__ unsigned long long block_excl_scan(unsigned long long v, unsigned lon
 // chunk totals the walk kernel accumulates into.
 // ===========================================================================
 __global__ void __launch_bounds__(CC_THREADS) k_cand_count(MeshView m, Work w) {
-    __shared__ unsigned long long s_warp[CC_THREADS / 32];
+    __shared__ unsigned long long s_warp[33];
     const int32_t gtid = blockIdx.x * CC_THREADS + threadIdx.x;
     for (int32_t i = gtid; i < w.n_chunk_max; i += gridDim.x * CC_THREADS) w.blk_b[i] = 0ull;
     const int32_t t0 = blockIdx.x * CC_TRI + threadIdx.x * CC_PER;  // 16 triangles per thread
-    uint32_t c = 0;
-    if (t0 < m.T) {
-        // flags is allocated to a multiple of 16 bytes: the int4 stays in bounds
-        const int4 v = *reinterpret_cast<const int4 *>(w.flags + t0);
-        const uint32_t wd[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
-#pragma unroll
-        for (int j = 0; j < CC_PER; j++)
-            if (t0 + j < m.T) c += __popc(starts_of((wd[j >> 2] >> (8 * (j & 3))) & 0xffu));
-    }
+    uint32_t st[4];
+    start_words(m, w, t0, st);
+    const uint32_t c = __popc(st[0]) + __popc(st[1]) + __popc(st[2]) + __popc(st[3]);
     unsigned long long total;
     block_excl_scan(c, s_warp, &total);
     if (threadIdx.x == 0) w.blk_a[blockIdx.x] = total;
@@ -92,12 +111,14 @@ __global__ void __launch_bounds__(CC_THREADS) k_cand_count(MeshView m, Work w) {
 // ===========================================================================
 // k_scan_blocks: one block, exclusive scan of n (read from *n_dev when n < 0)
 // 64-bit totals; *grand receives the sum.  Rounds of blockDim.x coalesced
-// entries with a running carry.
+// entries with a running carry.  With finish set (the chunk totals), thread
+// 0 then turns the grand total into P, N_F and offsets[P].
 // ===========================================================================
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned long long *in, unsigned long long *out,
                                                               int32_t n, const int32_t *n_dev, int32_t n_max,
-                                                              unsigned long long *grand) {
-    __shared__ unsigned long long s_warp[SCAN_THREADS / 32];
+                                                              unsigned long long *grand, MeshView m, Work w,
+                                                              int finish) {
+    __shared__ unsigned long long s_warp[33];
     if (n < 0) n = min(*n_dev, n_max);
     unsigned long long carry = 0;
     for (int32_t b = 0; b < n; b += SCAN_THREADS) {
@@ -108,7 +129,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned lon
         if (i < n) out[i] = carry + ex;
         carry += total;
     }
-    if (threadIdx.x == 0) *grand = carry;
+    if (threadIdx.x != 0) return;
+    *grand = carry;
+    if (!finish) return;
+    int32_t P = (int32_t)(carry >> 32);
+    const int64_t NF = (int64_t)(carry & 0xffffffffu);
+    if (P > m.T || NF > 3 * (int64_t)m.T) {
+        atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+        P = P > m.T ? m.T : P;
+    }
+    w.offsets[P] = (int32_t)NF;
+    w.ctrl->n_polygons = P;
+    w.ctrl->n_frontier = (int32_t)NF;
 }
 
 // ===========================================================================
@@ -117,30 +149,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned lon
 // 2048-start chunks for the kernels that follow.
 // ===========================================================================
 __global__ void __launch_bounds__(CC_THREADS) k_cand_write(MeshView m, Work w) {
-    __shared__ unsigned long long s_warp[CC_THREADS / 32];
+    __shared__ unsigned long long s_warp[33];
     const int32_t t0 = blockIdx.x * CC_TRI + threadIdx.x * CC_PER;
-    uint32_t wd[4] = {0u, 0u, 0u, 0u};
-    uint32_t c = 0;
-    if (t0 < m.T) {
-        const int4 v = *reinterpret_cast<const int4 *>(w.flags + t0);
-        wd[0] = (uint32_t)v.x; wd[1] = (uint32_t)v.y; wd[2] = (uint32_t)v.z; wd[3] = (uint32_t)v.w;
-#pragma unroll
-        for (int j = 0; j < CC_PER; j++)
-            if (t0 + j < m.T) c += __popc(starts_of((wd[j >> 2] >> (8 * (j & 3))) & 0xffu));
-    }
+    uint32_t st[4];
+    start_words(m, w, t0, st);
+    const uint32_t c = __popc(st[0]) + __popc(st[1]) + __popc(st[2]) + __popc(st[3]);
     unsigned long long total;
     int64_t pos = (int64_t)w.blk_a_pre[blockIdx.x] + (int64_t)block_excl_scan(c, s_warp, &total);
     const int32_t cap = 3 * m.T;
 #pragma unroll
-    for (int j = 0; j < CC_PER; j++) {
-        if (t0 + j >= m.T) break;
-        const uint32_t s = starts_of((wd[j >> 2] >> (8 * (j & 3))) & 0xffu);
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if ((s >> k) & 1u) {
-                if (pos < cap) w.cand[pos] = 3 * (t0 + j) + k;
-                pos++;
-            }
+    for (int i = 0; i < 4; i++) {
+        uint32_t bits = st[i];
+        while (bits) {
+            const int b = __ffs(bits) - 1;  // byte q = b / 8 (triangle t0 + 4i + q), corner k = b % 8
+            bits &= bits - 1u;
+            if (pos < cap) w.cand[pos] = 3 * (t0 + 4 * i + (b >> 3)) + (b & 7);
+            pos++;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -324,22 +348,6 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
     }
 }
 
-// ===========================================================================
-// finish: P, N_F and offsets[P] from the scanned chunk totals.
-// ===========================================================================
-__global__ void k_finish(MeshView m, Work w) {
-    const unsigned long long tot = w.ctrl->grand_b;
-    int32_t P = (int32_t)(tot >> 32);
-    const int64_t NF = (int64_t)(tot & 0xffffffffu);
-    if (P > m.T || NF > 3 * (int64_t)m.T) {
-        atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
-        P = P > m.T ? m.T : P;
-    }
-    w.offsets[P] = (int32_t)NF;
-    w.ctrl->n_polygons = P;
-    w.ctrl->n_frontier = (int32_t)NF;
-}
-
 int polygons_configure() { return 0; }
 
 int emit_blocks_per_sm() {
@@ -354,7 +362,7 @@ void launch_cand_count(const MeshView &m, const Work &w, cudaStream_t s) {
 
 void launch_cand_scan(const MeshView &m, const Work &w, cudaStream_t s) {
     k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(w.blk_a, w.blk_a_pre, w.n_cc_blocks, nullptr, 0,
-                                             &w.ctrl->n_cand64);
+                                             &w.ctrl->n_cand64, m, w, 0);
 }
 
 void launch_cand_write(const MeshView &m, const Work &w, cudaStream_t s) {
@@ -367,8 +375,7 @@ void launch_walk(const MeshView &m, const Work &w, cudaStream_t s) {
 
 void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s) {
     k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(w.blk_b, w.blk_b_pre, -1, &w.ctrl->n_chunks, w.n_chunk_max,
-                                             &w.ctrl->grand_b);
-    k_finish<<<1, 1, 0, s>>>(m, w);
+                                             &w.ctrl->grand_b, m, w, 1);
 }
 
 void launch_emit(const MeshView &m, const Work &w, cudaStream_t s) {

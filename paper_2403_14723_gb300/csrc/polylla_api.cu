@@ -20,7 +20,7 @@ const char *kStageNames[kStages] = {
     "longest_edge", "label_relink", "chords", "chord_links", "cand_count",
     "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack",
 };
-constexpr int kKernels = 11;       // chunk_scan launches two kernels
+constexpr int kKernels = 10;       // one kernel per stage
 constexpr int kBatchKernels = 4;   // pack; unpack; ranges (two kernels)
 
 }  // namespace

@@ -199,7 +199,7 @@ void launch_cand_count(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_cand_scan(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_cand_write(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_walk(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);  // two kernels
+void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_emit(const MeshView &m, const Work &w, cudaStream_t s);
 int polygons_configure();
 int emit_blocks_per_sm();

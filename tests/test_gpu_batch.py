@@ -94,7 +94,7 @@ def assert_batch_parity(meshes, db, g):
 def test_batch_matches_oracle_per_mesh():
     meshes = _mix()
     db, g = batch_run(meshes)
-    assert g["launches"] == 15
+    assert g["launches"] == 14
     assert_batch_parity(meshes, db, g)
 
 
@@ -146,7 +146,7 @@ def test_single_mesh_graph_and_tuning_keep_results():
             p.generate(stream)
             out = p.polygons(stream)
             stream.synchronize()
-            assert polylla.polylla_launch_count(p.ctx) == 11
+            assert polylla.polylla_launch_count(p.ctx) == 10
             assert np.array_equal(dm.next.cpu().numpy()[:3 * mesh.n_triangles], r.next_out[:3 * mesh.n_triangles])
             assert np.array_equal(out["he_list"].cpu().numpy(), r.he_list)
             assert np.array_equal(out["seeds"].cpu().numpy(), r.seeds)

@@ -183,4 +183,4 @@ def test_stage_timing_and_launch_count():
                            "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack"]
         assert all(v >= 0 for v in t.values())
         assert t["batch_pack"] == 0 and t["batch_unpack"] == 0
-        assert polylla.polylla_launch_count(p.ctx) == 11
+        assert polylla.polylla_launch_count(p.ctx) == 10
