@@ -145,28 +145,40 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned lon
 
 // ===========================================================================
 // k_cand_write: the walk starts of each block, in index order, at the
-// block's scanned offset.  Also stores the start count and the number of
+// block's scanned offset, staged in shared memory and stored coalesced.  Also stores the start count and the number of
 // 2048-start chunks for the kernels that follow.
 // ===========================================================================
 __global__ void __launch_bounds__(CC_THREADS) k_cand_write(MeshView m, Work w) {
     __shared__ unsigned long long s_warp[33];
+    __shared__ __align__(16) int32_t s_out[CW_BUF];
     const int32_t t0 = blockIdx.x * CC_TRI + threadIdx.x * CC_PER;
     uint32_t st[4];
     start_words(m, w, t0, st);
     const uint32_t c = __popc(st[0]) + __popc(st[1]) + __popc(st[2]) + __popc(st[3]);
     unsigned long long total;
-    int64_t pos = (int64_t)w.blk_a_pre[blockIdx.x] + (int64_t)block_excl_scan(c, s_warp, &total);
+    const int32_t ex = (int32_t)block_excl_scan(c, s_warp, &total);
+    const int64_t base = (int64_t)w.blk_a_pre[blockIdx.x];
     const int32_t cap = 3 * m.T;
+    // the block's starts go to shared memory in order, then out with
+    // coalesced stores; any past the buffer (more than CW_BUF starts in one
+    // block, not seen on the workloads measured) go out directly
+    int32_t k = ex;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         uint32_t bits = st[i];
         while (bits) {
             const int b = __ffs(bits) - 1;  // byte q = b / 8 (triangle t0 + 4i + q), corner k = b % 8
             bits &= bits - 1u;
-            if (pos < cap) w.cand[pos] = 3 * (t0 + 4 * i + (b >> 3)) + (b & 7);
-            pos++;
+            const int32_t e = 3 * (t0 + 4 * i + (b >> 3)) + (b & 7);
+            if (k < CW_BUF) s_out[k] = e;
+            else if (base + k < cap) w.cand[base + k] = e;
+            k++;
         }
     }
+    __syncthreads();
+    const int32_t nb = min((int32_t)total, CW_BUF);
+    for (int32_t i = threadIdx.x; i < nb; i += CC_THREADS)
+        if (base + i < cap) w.cand[base + i] = s_out[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int64_t nc = (int64_t)w.ctrl->n_cand64;  // written by the scan of the block counts
         if (nc > cap) {

@@ -102,6 +102,7 @@ struct BatchView {
 constexpr int CC_THREADS = 1024;
 constexpr int CC_PER = 16;
 constexpr int CC_TRI = CC_THREADS * CC_PER;
+constexpr int CW_BUF = 10240;  // walk starts a block stages in shared memory (40 KB)
 constexpr int SCAN_THREADS = 1024;
 constexpr int CHUNK = 2048;
 constexpr int WALK_THREADS = 256;
