@@ -389,8 +389,8 @@ def run_gb300(args):
         e_ms = dist_max(1e3 * (time.perf_counter() - t0) / e_steps, ws)
         assert p2 == P and nf2 == NF
         polylla.polylla_destroy(hctx)
-        h2d = 16 * V + 4 * 4 * H
-        d2h = 4 * (P + (P + 1) + 2 * NF + 2 * H) + 32
+        h2d = 16 * V + 2 * 4 * H                     # coords, origin, twin (next/prev are not read)
+        d2h = 4 * (P + (P + 1) + 2 * NF + 2 * 3 * T) + 32   # CSR, interior next/prev, control block
         e2e = {"value": ws * T / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "polylla_generate_host (pinned host buffers, copies inside the timed region)"}

@@ -178,10 +178,17 @@ int polylla_get_labels(polylla_ctx *ctx, polylla_labels *out, polylla_stream str
  * the mesh.  polylla_create_host allocates device arrays for a mesh of the
  * given sizes (no data yet); polylla_generate_host copies the host mesh in,
  * generates, and copies the polygons and the rewritten next/prev back.
- * Host buffers should be pinned (cudaHostAlloc) for full copy speed; any
- * host memory works.  Capacities of the outputs: seeds T, offsets T+1,
- * he_list and v_list 3T, next and prev H.  *n_polygons and *n_frontier
- * receive P and N_F.  Synchronizes stream before returning.
+ * Copies overlap the kernels where the method allows: twin is copied while
+ * the longest-edge stage runs on coords and origin, and next/prev (final
+ * after the repair) are copied back while the polygon output runs; the
+ * input next/prev are only copied (and the layout checked) when validate is
+ * nonzero, since the method does not read them; the border entries of the
+ * output next/prev are the input's, copied on the host.  Host buffers
+ * should be pinned (cudaHostAlloc) for full copy speed; any host memory
+ * works.  Capacities of the outputs: seeds T, offsets T+1, he_list and
+ * v_list 3T, next and prev H.  *n_polygons and *n_frontier receive P and
+ * N_F.  Synchronizes stream (and the context's side stream) before
+ * returning; not available while a graph is captured.
  */
 typedef struct {
     const double *coords;

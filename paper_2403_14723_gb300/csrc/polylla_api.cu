@@ -49,6 +49,12 @@ struct polylla_ctx {
     int32_t *meta = nullptr;           // [4 n_cap]
     int32_t *local_offsets = nullptr;  // [T_cap + n_cap + 1]
     size_t bytes = 0;                  // device bytes allocated
+    // host-buffer path: a side stream for copies that overlap the kernels,
+    // and the events that order them against the stages
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_twin = nullptr, ev_links = nullptr;
+    cudaEvent_t wait_before_relink = nullptr;  // enqueue: stage 1 waits for it
+    cudaEvent_t record_after_links = nullptr;  // enqueue: recorded after stage 3
     // captured generate (polylla_capture_graph)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -89,6 +95,12 @@ static void drop_graph(polylla_ctx *c) {
 
 static void free_all(polylla_ctx *c) {
     drop_graph(c);
+    if (c->aux) cudaStreamSynchronize(c->aux);
+    if (c->ev_twin) cudaEventDestroy(c->ev_twin);
+    if (c->ev_links) cudaEventDestroy(c->ev_links);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    c->aux = nullptr;
+    c->ev_twin = c->ev_links = nullptr;
     for (int i = 0; i < c->n_allocs; i++) cudaFree(c->allocs[i]);
     c->n_allocs = 0;
     if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -357,6 +369,12 @@ int polylla_create_host(polylla_ctx **out, int32_t n_vertices, int32_t n_triangl
     if (!rc && (rc = dev_alloc(c, &p, 4 * H)) == 0) c->mesh.next = (int32_t *)p;
     if (!rc && (rc = dev_alloc(c, &p, 4 * H)) == 0) c->mesh.prev = (int32_t *)p;
     if (!rc) rc = alloc_work(c, opt);
+    if (!rc) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_twin, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_links, cudaEventDisableTiming);
+        if (e != cudaSuccess) rc = cuda_fail(c, e);
+    }
     if (rc) {
         free_all(c);
         delete c;
@@ -389,9 +407,11 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
         launch_chunk_scan, launch_emit,
     };
     for (int i = 0; i < kCore; i++) {
+        if (i == 1 && c->wait_before_relink) CK(cudaStreamWaitEvent(s, c->wait_before_relink, 0));
         CK(begin(i));
         stages[i](c->mesh, c->w, s);
         CK(end(i));
+        if (i == 3 && c->record_after_links) CK(cudaEventRecord(c->record_after_links, s));
     }
     if (c->is_batch) {
         CK(begin(11));
@@ -500,35 +520,58 @@ int polylla_get_labels(polylla_ctx *c, polylla_labels *out, polylla_stream strea
 
 int polylla_generate_host(polylla_ctx *c, const polylla_host_mesh *in, polylla_host_result *out,
                           int32_t validate, polylla_stream stream) {
-    if (!c || !in || !out || !c->owns_mesh) return POLYLLA_ERR_INVALID_ARGUMENT;
+    if (!c || !in || !out || !c->owns_mesh || c->graph_exec) return POLYLLA_ERR_INVALID_ARGUMENT;
     if (!in->coords || !in->origin || !in->twin || !in->next || !in->prev) return POLYLLA_ERR_INVALID_ARGUMENT;
     if (!out->seeds || !out->offsets || !out->he_list || !out->v_list || !out->next || !out->prev)
         return POLYLLA_ERR_INVALID_ARGUMENT;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t H = (size_t)c->mesh.H, V = (size_t)c->mesh.V;
+    const size_t H = (size_t)c->mesh.H, V = (size_t)c->mesh.V, HI = 3 * (size_t)c->mesh.T;
+    // In: the longest-edge stage needs only coords and origin; twin comes
+    // in on the side stream meanwhile and the relink waits for it.  The
+    // method never reads next/prev, so they go in only for the layout check.
     CK(cudaMemcpyAsync((void *)c->mesh.xy, in->coords, 16 * V, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync((void *)c->mesh.origin, in->origin, 4 * H, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync((void *)c->mesh.twin, in->twin, 4 * H, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->mesh.next, in->next, 4 * H, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->mesh.prev, in->prev, 4 * H, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void *)c->mesh.twin, in->twin, 4 * H, cudaMemcpyHostToDevice, c->aux));
+    CK(cudaEventRecord(c->ev_twin, c->aux));
     if (validate) {
+        CK(cudaMemcpyAsync(c->mesh.next, in->next, 4 * H, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->mesh.prev, in->prev, 4 * H, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamWaitEvent(s, c->ev_twin, 0));
         int rc = run_validate(c, s);
         if (rc) return rc;
     }
-    int rc = polylla_generate(c, stream);
+    // the stages; next/prev are final after stage 3 and go out on the side
+    // stream while the polygon output stages run
+    c->wait_before_relink = c->ev_twin;
+    c->record_after_links = c->ev_links;
+    const bool timing = c->timing;
+    c->last_stream = s;
+    c->timed_last = timing;
+    int rc = enqueue(c, s, timing);
+    c->wait_before_relink = nullptr;
+    c->record_after_links = nullptr;
     if (rc) return rc;
+    CK(cudaStreamWaitEvent(c->aux, c->ev_links, 0));
+    CK(cudaMemcpyAsync(out->next, c->mesh.next, 4 * HI, cudaMemcpyDeviceToHost, c->aux));
+    CK(cudaMemcpyAsync(out->prev, c->mesh.prev, 4 * HI, cudaMemcpyDeviceToHost, c->aux));
+    // border half-edges are never written: their links are the input's
+    if (H > HI) {
+        memcpy(out->next + HI, in->next + HI, 4 * (H - HI));
+        memcpy(out->prev + HI, in->prev + HI, 4 * (H - HI));
+    }
     rc = read_ctrl(c, s);
-    if (rc) return rc;
-    rc = device_status(*c->h_ctrl);
-    if (rc) return rc;
+    if (rc == POLYLLA_OK) rc = device_status(*c->h_ctrl);
+    if (rc) {
+        cudaStreamSynchronize(c->aux);
+        return rc;
+    }
     const int32_t P = c->h_ctrl->n_polygons, NF = c->h_ctrl->n_frontier;
     CK(cudaMemcpyAsync(out->seeds, c->w.seeds, 4 * (size_t)P, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(out->offsets, c->w.offsets, 4 * (size_t)(P + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(out->he_list, c->w.he_list, 4 * (size_t)NF, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(out->v_list, c->w.v_list, 4 * (size_t)NF, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(out->next, c->mesh.next, 4 * H, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(out->prev, c->mesh.prev, 4 * H, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    CK(cudaStreamSynchronize(c->aux));
     out->n_polygons = P;
     out->n_frontier = NF;
     return POLYLLA_OK;
