@@ -687,11 +687,15 @@ def run_served(args):
         rc, lat, infos = srv.replay([hrs[i] for i in pick], t)
         assert rc == 0, f"served requests failed: {polylla.STATUS.get(rc, rc)}"
         span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        wait = np.array([i["t_admit"] - i["t_submit"] for i in infos])
+        serve = np.array([i["t_done"] - i["t_admit"] for i in infos])
         return {"requests": len(t), "triangles": int(tri[pick].sum()), "span_s": span,
+                "queue_ms": {"p50": 1e3 * float(np.percentile(wait, 50)), "p99": 1e3 * float(np.percentile(wait, 99))},
+                "service_ms": {"p50": 1e3 * float(np.percentile(serve, 50)), "p99": 1e3 * float(np.percentile(serve, 99))},
                 "tri_per_s": float(tri[pick].sum()) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_batch": float(np.mean([i["batch_meshes"] for i in infos])),
-                "h2d_bytes": int(sum(16 * pool[i].n_vertices + 16 * pool[i].n_halfedges for i in pick)),
-                "d2h_bytes": int(sum(4 * (2 * infos[k]["n_polygons"] + 1 + 2 * infos[k]["n_frontier"] + 2 * pool[i].n_halfedges)
+                "h2d_bytes": int(sum(16 * pool[i].n_vertices + 8 * pool[i].n_halfedges for i in pick)),
+                "d2h_bytes": int(sum(4 * (2 * infos[k]["n_polygons"] + 1 + 2 * infos[k]["n_frontier"] + 6 * pool[i].n_triangles)
                                      for k, i in enumerate(pick)))}
 
     with polylla.Server(memory_budget=r["budget"], n_slots=3) as srv:

@@ -346,6 +346,9 @@ typedef struct {
     int64_t device_bytes;        /* device memory held                             */
     int64_t batches, requests_done;
     double busy_seconds;         /* time with at least one batch in flight         */
+    double mean_in_ms;           /* per batch, on its stream: copies in,           */
+    double mean_run_ms;          /*   kernels and metadata readback,               */
+    double mean_out_ms;          /*   from metadata landed to results out          */
 } polylla_server_stats;
 
 /* Create a server on the current device (allocates all slots; starts the

@@ -236,30 +236,38 @@ __global__ void k_batch_seeds(int32_t *seeds, const int32_t *offsets, const int3
 // k_batch_meta (serving): per mesh i, meta[4i..4i+3] = {P_i, N_F,i, first
 // polygon, first CSR entry}, and each mesh's offsets rebased to start at 0
 // in local_offsets[poly_off[i] + i .. poly_off[i+1] + i] (P_i + 1 entries),
-// so that every mesh's CSR is four contiguous slices.
+// so that every mesh's CSR is four contiguous slices.  Grid-stride over all
+// P + n rebased entries (entry q belongs to the last mesh i with
+// poly_off[i] + i <= q), so one large mesh is spread over the whole grid.
 // ===========================================================================
 __global__ void k_batch_meta(BatchView b, const int32_t *offsets, const int32_t *poly_off, int32_t *local_offsets,
                              int32_t *meta) {
-    // one warp per mesh
-    const int32_t i = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= b.n) return;
-    const int32_t p0 = poly_off[i], p1 = poly_off[i + 1];
-    const int32_t c0 = offsets[p0], c1 = offsets[p1];
-    if (lane == 0) {
+    const int32_t n = b.n;
+    const int32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (int32_t i = gt; i < n; i += gs) {
+        const int32_t p0 = poly_off[i], p1 = poly_off[i + 1];
+        const int32_t c0 = offsets[p0];
         meta[4 * i] = p1 - p0;
-        meta[4 * i + 1] = c1 - c0;
+        meta[4 * i + 1] = offsets[p1] - c0;
         meta[4 * i + 2] = p0;
         meta[4 * i + 3] = c0;
     }
-    for (int32_t p = p0 + lane; p <= p1; p += 32) local_offsets[p + i] = offsets[p] - c0;
+    const int32_t total = poly_off[n] + n;
+    for (int32_t q = gt; q < total; q += gs) {
+        int32_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(poly_off + mid) + mid <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t p0 = __ldg(poly_off + lo);
+        local_offsets[q] = offsets[p0 + (q - p0 - lo)] - offsets[p0];
+    }
 }
 
 void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_off, int32_t *local_offsets,
                        int32_t *meta, cudaStream_t s) {
-    const int32_t warps_per_block = 8;
-    k_batch_meta<<<(b.n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
-        b, w.offsets, poly_off, local_offsets, meta);
+    k_batch_meta<<<w.persistent_blocks, 256, 0, s>>>(b, w.offsets, poly_off, local_offsets, meta);
 }
 
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,

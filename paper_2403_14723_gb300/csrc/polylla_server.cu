@@ -4,11 +4,13 @@
 // One scheduler thread owns every CUDA call.  Requests wait in a FIFO queue
 // in host memory; whenever a slot is free the scheduler takes, in arrival
 // order, as many waiting requests as fit the slot's capacity (meshes,
-// triangles, vertices, half-edges), copies their host arrays into the
-// slot's device arena, runs the batch (pack, the method's stages, unpack,
-// per-mesh metadata) and copies the per-mesh metadata back.  When that has
-// landed it copies each request's CSR slices and next/prev back into the
-// request's host buffers; when those land the requests complete.  Each
+// triangles, vertices, half-edges), copies their coords, origin and twin
+// into the slot's device arena (the method never reads next/prev), runs the
+// batch (pack, the method's stages, unpack, per-mesh metadata) and copies
+// the per-mesh metadata back.  When that has landed it copies each
+// request's CSR slices and interior next/prev back into the request's host
+// buffers (border entries are the input's, copied on the host); when those
+// land the requests complete.  Each
 // slot has its own stream, so one slot's copies overlap another's kernels.
 // Slots and arenas are allocated once, at create, within the memory budget:
 // admission against device memory is admission into a slot.
@@ -47,6 +49,9 @@ struct Slot {
     polylla_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_meta = nullptr, ev_out = nullptr;
+    // timing of the batch in flight: start, inputs in, metadata out, results out
+    cudaEvent_t ev_t0 = nullptr, ev_in = nullptr, ev_tm = nullptr, ev_to = nullptr;
+    double host_meta_seen = 0;  // when the scheduler saw the metadata land
     double *coords = nullptr;  // device arena: concatenated local arrays
     int32_t *origin = nullptr, *twin = nullptr, *next = nullptr, *prev = nullptr;
     int32_t *h_off = nullptr;  // pinned [4 (n_cap + 1)]: v, t, h, b prefix sums
@@ -88,8 +93,9 @@ struct polylla_server {
     bool stop = false;
     std::thread sched;
 
-    int64_t batches = 0, done_count = 0;
+    int64_t batches = 0, done_count = 0, timed_batches = 0;
     double busy = 0.0;
+    double t_in = 0, t_run = 0, t_out = 0;  // summed ms: copies in, kernels + metadata, results out
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void loop();
@@ -159,7 +165,7 @@ bool polylla_server::launch(Slot &s) {
         q->t_admit = t;
         q->batch_meshes = n;
     }
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(s.ev_t0, s.stream);
     for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
         const polylla_request &r = take[i]->r;
         const size_t Hb = 4 * (size_t)r.n_halfedges;
@@ -167,9 +173,10 @@ bool polylla_server::launch(Slot &s) {
                             cudaMemcpyHostToDevice, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.origin + ho[i], r.mesh.origin, Hb, cudaMemcpyHostToDevice, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.twin + ho[i], r.mesh.twin, Hb, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.next + ho[i], r.mesh.next, Hb, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.prev + ho[i], r.mesh.prev, Hb, cudaMemcpyHostToDevice, s.stream);
+        // next/prev are not read by the method (their interior entries are
+        // rewritten, border entries go back from the host input)
     }
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev_in, s.stream);
     int rc = e == cudaSuccess ? serve_run(s.ctx, n, vo[n], to[n], ho[n], s.h_off, s.stream) : POLYLLA_ERR_CUDA;
     if (rc == POLYLLA_OK) {
         ServeOutputs o;
@@ -177,6 +184,7 @@ bool polylla_server::launch(Slot &s) {
         e = cudaMemcpyAsync(s.h_meta, o.meta, 16 * (size_t)n, cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_ctrl, o.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev_meta, s.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(s.ev_tm, s.stream);
         if (e != cudaSuccess) rc = POLYLLA_ERR_CUDA;
     }
     if (rc != POLYLLA_OK) {
@@ -218,10 +226,17 @@ void polylla_server::copy_out(Slot &s) {
                                 s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out.he_list, o.he_list + c0, 4 * (size_t)NF, cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out.v_list, o.v_list + c0, 4 * (size_t)NF, cudaMemcpyDeviceToHost, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(out.next, s.next + ho[i], Hb, cudaMemcpyDeviceToHost, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(out.prev, s.prev + ho[i], Hb, cudaMemcpyDeviceToHost, s.stream);
+        const size_t HIb = 12 * (size_t)q->r.n_triangles;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.next, s.next + ho[i], HIb, cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.prev, s.prev + ho[i], HIb, cudaMemcpyDeviceToHost, s.stream);
+        if (Hb > HIb) {
+            const size_t n_int = 3 * (size_t)q->r.n_triangles;
+            memcpy(out.next + n_int, q->r.mesh.next + n_int, Hb - HIb);
+            memcpy(out.prev + n_int, q->r.mesh.prev + n_int, Hb - HIb);
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecord(s.ev_out, s.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev_to, s.stream);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s.stream);
         finish(s, POLYLLA_ERR_CUDA);
@@ -251,6 +266,18 @@ void polylla_server::loop() {
             if (s.state == 2) {
                 const cudaError_t q = cudaEventQuery(s.ev_out);
                 if (q == cudaSuccess || q != cudaErrorNotReady) {
+                    if (q == cudaSuccess) {
+                        float a = 0, b = 0, c = 0;
+                        if (cudaEventElapsedTime(&a, s.ev_t0, s.ev_in) == cudaSuccess &&
+                            cudaEventElapsedTime(&b, s.ev_in, s.ev_tm) == cudaSuccess &&
+                            cudaEventElapsedTime(&c, s.ev_tm, s.ev_to) == cudaSuccess) {
+                            std::lock_guard<std::mutex> g(mu);
+                            t_in += a;
+                            t_run += b;
+                            t_out += c;
+                            timed_batches++;
+                        }
+                    }
                     for (Req *r : s.reqs) {
                         r->r.result.n_polygons = r->P;
                         r->r.result.n_frontier = r->NF;
@@ -299,6 +326,8 @@ static void free_slot(Slot &s) {
     if (s.h_meta) cudaFreeHost(s.h_meta);
     if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
     if (s.ev_meta) cudaEventDestroy(s.ev_meta);
+    for (cudaEvent_t ev : {s.ev_t0, s.ev_in, s.ev_tm, s.ev_to})
+        if (ev) cudaEventDestroy(ev);
     if (s.ev_out) cudaEventDestroy(s.ev_out);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
@@ -312,6 +341,10 @@ static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t
     cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_meta, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_in);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_tm);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_to);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.coords, 16 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.origin, 4 * (size_t)H);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.twin, 4 * (size_t)H);
@@ -462,6 +495,10 @@ int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out) {
     out->batches = srv->batches;
     out->requests_done = srv->done_count;
     out->busy_seconds = srv->busy;
+    const double nb = srv->timed_batches > 0 ? (double)srv->timed_batches : 1.0;
+    out->mean_in_ms = srv->t_in / nb;
+    out->mean_run_ms = srv->t_run / nb;
+    out->mean_out_ms = srv->t_out / nb;
     return POLYLLA_OK;
 }
 
