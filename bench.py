@@ -56,6 +56,9 @@ def parse():
                     help="length of the served request trace (served workload)")
     ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
                     help="trace length replayed through the one-mesh-at-a-time server")
+    ap.add_argument("--serve-slots", type=int, default=3, help="batches in flight (served workload)")
+    ap.add_argument("--serve-batch-triangles", type=int, default=0,
+                    help="triangles at which a served batch stops growing (0: slot capacity)")
     return ap.parse_args()
 
 
@@ -698,7 +701,8 @@ def run_served(args):
                 "d2h_bytes": int(sum(4 * (2 * infos[k]["n_polygons"] + 1 + 2 * infos[k]["n_frontier"] + 6 * pool[i].n_triangles)
                                      for k, i in enumerate(pick)))}
 
-    with polylla.Server(memory_budget=r["budget"], n_slots=3) as srv:
+    with polylla.Server(memory_budget=r["budget"], n_slots=args.serve_slots,
+                        max_batch_triangles=args.serve_batch_triangles) as srv:
         replay(srv, 1.0, seed=1000 + rank)                     # warm-up, untimed
         dist_barrier(ws)
         st0 = srv.stats()
@@ -727,6 +731,7 @@ def run_served(args):
                               f"{int(100 * r['p_large'])}% log-uniform {r['large']}; Delaunay and perturbed grids",
                        "pool": f"{len(small)} small + {len(large)} large seeded meshes in pinned host memory",
                        "memory_budget_bytes": r["budget"], "slots": st["n_slots"],
+                       "max_batch_triangles": args.serve_batch_triangles,
                        "slot_triangles": st["slot_triangles"], "device_bytes": st["device_bytes"],
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},

@@ -328,6 +328,9 @@ typedef struct {
     int32_t n_slots;           /* batches in flight, >= 1 (0: 3)                 */
     int32_t max_batch_meshes;  /* meshes per batch, >= 1 (0: 4096)               */
     int32_t max_rotation;      /* as polylla_options (0: 4096)                   */
+    int32_t max_batch_triangles; /* a batch stops growing past this many
+                                    triangles (0: the slot's capacity); a single
+                                    larger request still runs, alone          */
 } polylla_server_options;
 typedef struct {
     int32_t n_vertices, n_triangles, n_halfedges;

@@ -80,6 +80,7 @@ struct polylla_server {
     int device = 0;
     int32_t max_batch = 4096;
     int32_t max_rotation = 0;
+    int64_t max_batch_tri = 0;  // 0: slot capacity
     int n_slots = 0;
     Slot slots[kMaxSlots];
     int64_t device_bytes = 0;
@@ -141,6 +142,7 @@ bool polylla_server::launch(Slot &s) {
                 continue;
             }
             if (V + r.n_vertices > s.V_cap || T + r.n_triangles > s.T_cap || H + r.n_halfedges > s.H_cap) break;
+            if (!take.empty() && max_batch_tri > 0 && T + r.n_triangles > max_batch_tri) break;
             V += r.n_vertices;
             T += r.n_triangles;
             H += r.n_halfedges;
@@ -366,7 +368,7 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
     if (!out) return POLYLLA_ERR_INVALID_ARGUMENT;
     *out = nullptr;
     if (!opt || opt->memory_budget <= 0 || opt->n_slots < 0 || opt->n_slots > kMaxSlots || opt->max_batch_meshes < 0 ||
-        opt->max_rotation < 0)
+        opt->max_rotation < 0 || opt->max_batch_triangles < 0)
         return POLYLLA_ERR_INVALID_ARGUMENT;
     polylla_server *srv = new (std::nothrow) polylla_server();
     if (!srv) return POLYLLA_ERR_OUT_OF_MEMORY;
@@ -377,6 +379,7 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
     srv->n_slots = opt->n_slots ? opt->n_slots : 3;
     srv->max_batch = opt->max_batch_meshes ? opt->max_batch_meshes : 4096;
     srv->max_rotation = opt->max_rotation;
+    srv->max_batch_tri = opt->max_batch_triangles;
     // slot capacity: the largest T whose slot, with V <= T + 2n and
     // H <= 4T + 2n (bounds for triangulated disks), fits budget / n_slots
     const int64_t per = opt->memory_budget / srv->n_slots;

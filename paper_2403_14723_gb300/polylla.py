@@ -86,7 +86,8 @@ class polylla_tuning(ctypes.Structure):
 
 class polylla_server_options(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_int64), ("n_slots", ctypes.c_int32),
-                ("max_batch_meshes", ctypes.c_int32), ("max_rotation", ctypes.c_int32)]
+                ("max_batch_meshes", ctypes.c_int32), ("max_rotation", ctypes.c_int32),
+                ("max_batch_triangles", ctypes.c_int32)]
 
 
 class polylla_request(ctypes.Structure):
@@ -521,9 +522,11 @@ class Server:
     """The serving loop (``polylla_server_*``): continuous batching of host
     requests on the current device."""
 
-    def __init__(self, memory_budget: int, n_slots: int = 3, max_batch_meshes: int = 0, max_rotation: int = 0):
+    def __init__(self, memory_budget: int, n_slots: int = 3, max_batch_meshes: int = 0, max_rotation: int = 0,
+                 max_batch_triangles: int = 0):
         lib = load_library()
-        opt = polylla_server_options(int(memory_budget), int(n_slots), int(max_batch_meshes), int(max_rotation))
+        opt = polylla_server_options(int(memory_budget), int(n_slots), int(max_batch_meshes), int(max_rotation),
+                                     int(max_batch_triangles))
         h = ctypes.c_void_p()
         _check(lib.polylla_server_create(ctypes.byref(h), ctypes.byref(opt)), "polylla_server_create")
         self.h = h.value

@@ -78,9 +78,9 @@ def test_null_arguments_rejected_without_gpu(lib_path):
     srv = ctypes.c_void_p()
     assert lib.polylla_server_create(None, None) == -1
     assert lib.polylla_server_create(ctypes.byref(srv), None) == -1
-    bad = polylla.polylla_server_options(0, 3, 0, 0)                     # no memory budget
+    bad = polylla.polylla_server_options(0, 3, 0, 0, 0)                  # no memory budget
     assert lib.polylla_server_create(ctypes.byref(srv), ctypes.byref(bad)) == -1
-    bad = polylla.polylla_server_options(1 << 30, 99, 0, 0)              # too many slots
+    bad = polylla.polylla_server_options(1 << 30, 99, 0, 0, 0)           # too many slots
     assert lib.polylla_server_create(ctypes.byref(srv), ctypes.byref(bad)) == -1
     assert lib.polylla_server_submit(None, None, None) == -1
     assert lib.polylla_server_get_stats(None, None) == -1
