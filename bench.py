@@ -422,7 +422,8 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f64/int32", "data": "synthetic",
             "config": {"workload": args.workload, "triangles": T, "vertices": V, "halfedges": H,
                        "polygons": P, "frontier_halfedges": NF, "parallelism": f"replicas x{ws}",
-                       "l2": "256 MiB buffer written between timed steps; inputs (1.07 GB) exceed L2"},
+                       "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
+                             f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
             "kernel_digest": kernel_digest(),
@@ -610,7 +611,8 @@ def run_batched(args):
                        "sizes": f"log-uniform [{r['t_min']}, {r['t_max']}] triangles, seed {r['seed']}; "
                                 "even meshes Delaunay of uniform points, odd perturbed grids (jitter 0.3)",
                        "parallelism": f"replicas x{ws}", "cuda_graph": True, "tuning": tuning,
-                       "l2": "256 MiB buffer written between timed steps; inputs exceed L2"},
+                       "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
+                             f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "one_mesh_at_a_time": {"value": ws * T / (ms_loop * 1e-3), "unit": UNIT, "ms_per_step": ms_loop,
                                    "launches_per_step": 10 * n_meshes,
                                    "how": "polylla_generate per mesh, back to back on one stream"},
