@@ -64,6 +64,12 @@ def test_null_arguments_rejected_without_gpu(lib_path):
     assert lib.polylla_create(ctypes.byref(ctx), ctypes.byref(m), None, None) == -1
     assert lib.polylla_generate(None, None) == -1
     assert lib.polylla_get_polygons(None, None, None) == -1
+    m = polylla.polylla_mesh(3, 0, 3, 16, 16, 16, 16, 16)                # no triangles
+    assert lib.polylla_create(ctypes.byref(ctx), ctypes.byref(m), None, None) == -1
+    T = 715_827_883                                                      # 3T no longer fits int32
+    m = polylla.polylla_mesh(T + 2, T, 2 ** 31 - 1, 16, 16, 16, 16, 16)
+    assert lib.polylla_create(ctypes.byref(ctx), ctypes.byref(m), None, None) == -1
+    assert lib.polylla_create_host(ctypes.byref(ctx), 3, 0, 3, None) == -1
     assert lib.polylla_batch_create(None, None, None, None) == -1
     assert lib.polylla_batch_create(ctypes.byref(ctx), None, None, None) == -1
     one = np.array([0, 3], dtype=np.int32)

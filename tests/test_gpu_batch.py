@@ -151,3 +151,15 @@ def test_single_mesh_graph_and_tuning_keep_results():
             assert np.array_equal(out["he_list"].cpu().numpy(), r.he_list)
             assert np.array_equal(out["seeds"].cpu().numpy(), r.seeds)
     polylla.polylla_tuning_cache_clear()
+
+
+def test_batch_4096_full_size_matches_oracle():
+    """The batched workload at full size (4,096 meshes, 111M triangles), in
+    the launch configuration bench.py times (autotuned, from a CUDA graph):
+    every mesh against its own oracle run."""
+    import bench
+
+    meshes = bench.batch_meshes(4096)
+    db, g = batch_run(meshes, graph=True, tune=True)
+    assert_batch_parity(meshes, db, g)
+    polylla.polylla_tuning_cache_clear()

@@ -89,3 +89,26 @@ def test_request_larger_than_a_slot_fails_cleanly():
         hr = polylla.HostRequest(small)
         info = srv.wait(srv.submit(hr))
         _check(small, info, hr.result(info), oracle.run_mesh(small), "after a rejected request")
+
+
+def test_served_recipe_pool_matches_oracle():
+    """The served workload's request pool (512 small + 32 large meshes, up
+    to 8M triangles) through one second of its Poisson trace in the server
+    configuration bench.py times: every pool mesh a request used gets the
+    oracle's result."""
+    import bench
+
+    build.build_library()
+    small, large = bench.serve_pool()
+    pool = small + large
+    hrs = [polylla.HostRequest(m) for m in pool]
+    t, pick = bench.serve_trace(1.0, len(small), len(large), seed=11)
+    with polylla.Server(memory_budget=bench.SERVE_RECIPE["budget"], n_slots=3) as srv:
+        rc, lat, infos = srv.replay([hrs[i] for i in pick], t)
+    assert rc == 0 and np.all(lat > 0)
+    last = {}
+    for k, i in enumerate(pick):
+        last[int(i)] = infos[k]
+    assert any(i >= len(small) for i in last), "no large request in the trace"
+    for i, info in sorted(last.items()):
+        _check(pool[i], info, hrs[i].result(info), oracle.run_mesh(pool[i]), f"pool mesh {i} ({pool[i].name})")
