@@ -186,14 +186,22 @@ def kernel_digest() -> str:
     return build._digest()
 
 
+def core_kernel_digest() -> str:
+    from paper_2403_14723_gb300 import build
+
+    return build.core_digest()
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary,
     if it was taken on the current kernel sources (else None)."""
+    from paper_2403_14723_gb300 import build
+
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_digest") != kernel_digest():
+    if d.get("core_kernel_digest") != build.core_digest():
         return None
     k = d.get("kernels", {}).get(kernel)
     if not k:
@@ -426,7 +434,7 @@ def run_gb300(args):
                              f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
-            "kernel_digest": kernel_digest(),
+            "kernel_digest": kernel_digest(), "core_kernel_digest": core_kernel_digest(),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -32,6 +32,22 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpolylla")
 
 
+# the files that define the method's kernels (their DRAM traffic, recorded
+# from ncu, stays valid while these are unchanged)
+CORE_SOURCES = ["kernels_label.cu", "kernels_repair.cu", "kernels_output.cu", "polylla_internal.cuh"]
+
+
+def core_digest() -> str:
+    """Digest of the method's kernel sources and compile flags."""
+    h = hashlib.sha1()
+    for s in CORE_SOURCES:
+        with open(os.path.join(CSRC, s), "rb") as fh:
+            h.update(fh.read())
+    flags = [f for f in NVCC_FLAGS if not f.startswith("-I")]
+    h.update(" ".join(ARCH + flags).encode())
+    return h.hexdigest()[:12]
+
+
 def _digest(extra=()) -> str:
     h = hashlib.sha1()
     for f in [os.path.join(CSRC, s) for s in SOURCES] + HEADERS:
