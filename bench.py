@@ -521,7 +521,7 @@ def run_batched(args):
             ms = timed(args.steps, step)
         dist_barrier(ws)
         ms = dist_max(ms, ws)
-        launches = args.steps * 14
+        launches = args.steps * 15
         out = polylla.polylla_get_polygons(ctx, stream)
         P, NF = out["n_polygons"], out["n_frontier"]
         po = polylla.polylla_batch_polygon_offsets(ctx, n_meshes).cpu().numpy()
@@ -752,7 +752,7 @@ def run_served(args):
                     "d2h_bytes_per_step": main["d2h_bytes"] // max(1, main["requests"]),
                     "api": "polylla_server_replay: host meshes in, host results out, per request"},
             "roofline": None, "cpu_baseline": None,
-            "gpu_launches": batches * 15, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
+            "gpu_launches": batches * 16, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -214,7 +214,7 @@ int polylla_generate_host(polylla_ctx *ctx, const polylla_host_mesh *in,
  * polylla_stage_name gives the name of stage i: the ten stages of the
  * method, then "batch_pack" and "batch_unpack".
  * polylla_launch_count gives the number of kernels the last generate
- * launched (10 for a mesh, 14 for a batch).
+ * launched (10 for a mesh, 15 for a batch).
  */
 int polylla_set_timing(polylla_ctx *ctx, int32_t enable);
 int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
@@ -268,7 +268,7 @@ int polylla_batch_polygon_offsets(polylla_ctx *ctx, const int32_t **poly_offset)
  * context (its kernels, with the current launch settings) into a CUDA graph
  * on stream (which must not be NULL, the legacy stream cannot be captured);
  * from then on polylla_generate launches that graph, one launch instead of
- * 10 or 14, untimed.  Changing the launch settings (polylla_set_tuning,
+ * 10 or 15, untimed.  Changing the launch settings (polylla_set_tuning,
  * polylla_autotune) or polylla_release_graph drops the graph.  The graph
  * reads and writes the same device arrays as the captured generate.
  */

@@ -81,18 +81,21 @@ __device__ bool pack_table(const BatchView &b, bool border, int32_t base, int32_
 
 // ===========================================================================
 // k_batch_pack: union origin/twin (and next/prev when given) from the local
-// arrays.  Blocks [0, nbI) cover interior union half-edges, the rest the
-// border ones; a block tabulates the meshes its range touches and each
+// arrays.  Logical blocks [0, nbI) cover interior union half-edges, the rest
+// the border ones (blk0 offsets the launch, so the border blocks can run on
+// their own); a block tabulates the meshes its range touches and each
 // element finds its mesh there.  With bad != nullptr every local value is
 // range-checked (create).
 // ===========================================================================
 __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t *u_origin, int32_t *u_twin,
-                                                           int32_t *u_next, int32_t *u_prev, int32_t *bad) {
+                                                           int32_t *u_next, int32_t *u_prev, int32_t *bad,
+                                                           int32_t blk0) {
     __shared__ PackTable tb;
     const int32_t HI = 3 * b.T_tot;
     const int32_t nbI = (HI + BP_SPAN - 1) / BP_SPAN;
-    const bool border = (int32_t)blockIdx.x >= nbI;
-    const int32_t base = border ? HI + ((int32_t)blockIdx.x - nbI) * BP_SPAN : (int32_t)blockIdx.x * BP_SPAN;
+    const int32_t blk = (int32_t)blockIdx.x + blk0;
+    const bool border = blk >= nbI;
+    const int32_t base = border ? HI + (blk - nbI) * BP_SPAN : blk * BP_SPAN;
     const int32_t end = min(base + BP_SPAN, border ? b.H_tot : HI);
     const bool tabled = pack_table(b, border, base, end, tb);
     // all loads of the thread's items first, then all stores: the stores
@@ -157,6 +160,78 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t 
         }
     }
     if (fail) atomicOr(bad, 1);
+}
+
+// ===========================================================================
+// k_batch_pack4 (generate path, interior only): each thread packs runs of 4
+// consecutive union half-edges and stores them with one 16-byte store per
+// array; the border tail is left to k_batch_pack.
+// ===========================================================================
+constexpr int BP4_RUNS = 2;  // runs of 4 per thread
+constexpr int BP4_SPAN = BP_THREADS * 4 * BP4_RUNS;
+__global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t *u_origin, int32_t *u_twin) {
+    __shared__ PackTable tb;
+    const int32_t HI = 3 * b.T_tot;
+    const int32_t base = (int32_t)blockIdx.x * BP4_SPAN;
+    const int32_t end = min(base + BP4_SPAN, HI);
+    const bool tabled = pack_table(b, false, base, end, tb);
+    int32_t o[BP4_RUNS][4], tw[BP4_RUNS][4], jj[BP4_RUNS][4];
+    int32_t j = 0;
+#pragma unroll
+    for (int r = 0; r < BP4_RUNS; r++) {
+        const int32_t x0 = base + 4 * (r * BP_THREADS + (int32_t)threadIdx.x);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int32_t x = x0 + q;
+            jj[r][q] = -1;
+            if (x >= end) continue;
+            int32_t g;
+            if (tabled) {
+                while (tb.start[j + 1] <= x) j++;
+                g = x + tb.to_local[j];
+                jj[r][q] = j;
+            } else {
+                const int32_t m = seg_of(b.t_off, b.n, x / 3);
+                g = b.h_off[m] + (x - 3 * b.t_off[m]);
+                jj[r][q] = m;
+            }
+            o[r][q] = b.origin[g];
+            tw[r][q] = b.twin[g];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < BP4_RUNS; r++) {
+        const int32_t x0 = base + 4 * (r * BP_THREADS + (int32_t)threadIdx.x);
+        int32_t uo[4], ut[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            uo[q] = 0;
+            ut[q] = 0;
+            if (jj[r][q] < 0) continue;
+            int32_t t3, ti3, bo, v0;
+            if (tabled) {
+                const int32_t p = jj[r][q];
+                t3 = tb.t3[p]; ti3 = tb.ti3[p]; bo = tb.bo[p]; v0 = tb.v0[p];
+            } else {
+                const int32_t m = jj[r][q];
+                const int32_t t0 = b.t_off[m], Ti = b.t_off[m + 1] - t0;
+                t3 = 3 * t0; ti3 = 3 * Ti; bo = HI + b.b_off[m] - 3 * Ti; v0 = b.v_off[m];
+            }
+            uo[q] = o[r][q] + v0;
+            ut[q] = tw[r][q] < ti3 ? t3 + tw[r][q] : bo + tw[r][q];
+        }
+        if (x0 + 3 < end) {
+            *reinterpret_cast<int4 *>(u_origin + x0) = make_int4(uo[0], uo[1], uo[2], uo[3]);
+            *reinterpret_cast<int4 *>(u_twin + x0) = make_int4(ut[0], ut[1], ut[2], ut[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (x0 + q < end) {
+                    u_origin[x0 + q] = uo[q];
+                    u_twin[x0 + q] = ut[q];
+                }
+        }
+    }
 }
 
 // ===========================================================================
@@ -273,8 +348,15 @@ void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_of
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
                        int32_t *bad, cudaStream_t s) {
     const int32_t HI = 3 * b.T_tot, HB = b.H_tot - HI;
+    if (!u_next && !bad) {
+        // interior by runs of 4, border by the general kernel (its border blocks only)
+        k_batch_pack4<<<(HI + BP4_SPAN - 1) / BP4_SPAN, BP_THREADS, 0, s>>>(b, u_origin, u_twin);
+        const int32_t nbI = (HI + BP_SPAN - 1) / BP_SPAN, nbB = (HB + BP_SPAN - 1) / BP_SPAN;
+        if (nbB > 0) k_batch_pack<<<nbB, BP_THREADS, 0, s>>>(b, u_origin, u_twin, nullptr, nullptr, nullptr, nbI);
+        return;
+    }
     const int32_t blocks = (HI + BP_SPAN - 1) / BP_SPAN + (HB + BP_SPAN - 1) / BP_SPAN;
-    k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad);
+    k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad, 0);
 }
 
 void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s) {

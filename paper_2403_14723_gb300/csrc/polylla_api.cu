@@ -21,7 +21,7 @@ const char *kStageNames[kStages] = {
     "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack",
 };
 constexpr int kKernels = 10;       // one kernel per stage
-constexpr int kBatchKernels = 4;   // pack; unpack; ranges (two kernels)
+constexpr int kBatchKernels = 5;   // pack (interior, border); unpack; ranges (two kernels)
 
 }  // namespace
 
