@@ -321,6 +321,13 @@ int polylla_tuning_cache_clear(void);
  * mesh's own indices, written to the request's host buffers (capacities as
  * polylla_generate_host).  The host arrays of a request must stay valid
  * and unchanged until it completes.
+ *
+ * Requests are not layout-checked (that would cost a pass per batch), but
+ * every origin and twin is range-checked while a batch is packed: an index
+ * outside its mesh is replaced by one inside it, so no kernel reads outside
+ * the batch's arrays, and the batch completes with POLYLLA_ERR_INVALID_MESH
+ * (every request in it: device errors are per batch).  The same holds for
+ * polylla_generate on a batch created without validation.
  */
 typedef struct polylla_server polylla_server;
 typedef struct {

@@ -84,12 +84,15 @@ __device__ bool pack_table(const BatchView &b, bool border, int32_t base, int32_
 // arrays.  Logical blocks [0, nbI) cover interior union half-edges, the rest
 // the border ones (blk0 offsets the launch, so the border blocks can run on
 // their own); a block tabulates the meshes its range touches and each
-// element finds its mesh there.  With bad != nullptr every local value is
-// range-checked (create).
+// element finds its mesh there.  Every origin and twin is range-checked:
+// one outside its mesh is replaced by an index inside it (vertex 0, the
+// mesh's first border half-edge), so no later kernel can leave the mesh,
+// and the run is flagged (input_err); with bad != nullptr (create) next and
+// prev are checked too and bad is set.
 // ===========================================================================
 __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t *u_origin, int32_t *u_twin,
                                                            int32_t *u_next, int32_t *u_prev, int32_t *bad,
-                                                           int32_t blk0) {
+                                                           int32_t *input_err, int32_t blk0) {
     __shared__ PackTable tb;
     const int32_t HI = 3 * b.T_tot;
     const int32_t nbI = (HI + BP_SPAN - 1) / BP_SPAN;
@@ -150,7 +153,14 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t 
             hi = b.h_off[m + 1] - b.h_off[m];
             vi = b.v_off[m + 1] - v0;
         }
-        if (bad) fail |= o[k] < 0 || o[k] >= vi || tw[k] < 0 || tw[k] >= hi;
+        const bool out = o[k] < 0 || o[k] >= vi || tw[k] < 0 || tw[k] >= hi;
+        fail |= out;
+        if (out) {
+            // keep every later access inside the mesh: vertex 0, and the
+            // mesh's first border half-edge (a twin that stops rotations)
+            if (o[k] < 0 || o[k] >= vi) o[k] = 0;
+            if (tw[k] < 0 || tw[k] >= hi) tw[k] = ti3;
+        }
         u_origin[x] = o[k] + v0;
         u_twin[x] = tw[k] < ti3 ? t3 + tw[k] : bo + tw[k];
         if (u_next) {
@@ -159,7 +169,10 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t 
             u_prev[x] = pv[k] < ti3 ? t3 + pv[k] : bo + pv[k];
         }
     }
-    if (fail) atomicOr(bad, 1);
+    if (fail) {
+        if (bad) atomicOr(bad, 1);
+        if (input_err) atomicOr(input_err, 1);
+    }
 }
 
 // ===========================================================================
@@ -169,14 +182,15 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t 
 // ===========================================================================
 constexpr int BP4_RUNS = 2;  // runs of 4 per thread
 constexpr int BP4_SPAN = BP_THREADS * 4 * BP4_RUNS;
-__global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t *u_origin, int32_t *u_twin) {
+__global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t *u_origin, int32_t *u_twin,
+                                                            int32_t *input_err) {
     __shared__ PackTable tb;
     const int32_t HI = 3 * b.T_tot;
     const int32_t base = (int32_t)blockIdx.x * BP4_SPAN;
     const int32_t end = min(base + BP4_SPAN, HI);
     const bool tabled = pack_table(b, false, base, end, tb);
     int32_t o[BP4_RUNS][4], tw[BP4_RUNS][4], jj[BP4_RUNS][4];
-    int32_t j = 0;
+    int32_t j = 0, fail = 0;
 #pragma unroll
     for (int r = 0; r < BP4_RUNS; r++) {
         const int32_t x0 = base + 4 * (r * BP_THREADS + (int32_t)threadIdx.x);
@@ -208,17 +222,22 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t
             uo[q] = 0;
             ut[q] = 0;
             if (jj[r][q] < 0) continue;
-            int32_t t3, ti3, bo, v0;
+            int32_t t3, ti3, bo, v0, hi, vi;
             if (tabled) {
                 const int32_t p = jj[r][q];
-                t3 = tb.t3[p]; ti3 = tb.ti3[p]; bo = tb.bo[p]; v0 = tb.v0[p];
+                t3 = tb.t3[p]; ti3 = tb.ti3[p]; bo = tb.bo[p]; v0 = tb.v0[p]; hi = tb.hi[p]; vi = tb.vi[p];
             } else {
                 const int32_t m = jj[r][q];
                 const int32_t t0 = b.t_off[m], Ti = b.t_off[m + 1] - t0;
                 t3 = 3 * t0; ti3 = 3 * Ti; bo = HI + b.b_off[m] - 3 * Ti; v0 = b.v_off[m];
+                hi = b.h_off[m + 1] - b.h_off[m]; vi = b.v_off[m + 1] - v0;
             }
-            uo[q] = o[r][q] + v0;
-            ut[q] = tw[r][q] < ti3 ? t3 + tw[r][q] : bo + tw[r][q];
+            int32_t ov = o[r][q], tv = tw[r][q];
+            // out-of-range indices are flagged and kept inside the mesh
+            if (ov < 0 || ov >= vi) { ov = 0; fail = 1; }
+            if (tv < 0 || tv >= hi) { tv = ti3; fail = 1; }
+            uo[q] = ov + v0;
+            ut[q] = tv < ti3 ? t3 + tv : bo + tv;
         }
         if (x0 + 3 < end) {
             *reinterpret_cast<int4 *>(u_origin + x0) = make_int4(uo[0], uo[1], uo[2], uo[3]);
@@ -232,6 +251,7 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t
                 }
         }
     }
+    if (fail && input_err) atomicOr(input_err, 1);
 }
 
 // ===========================================================================
@@ -346,17 +366,18 @@ void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_of
 }
 
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
-                       int32_t *bad, cudaStream_t s) {
+                       int32_t *bad, int32_t *input_err, cudaStream_t s) {
     const int32_t HI = 3 * b.T_tot, HB = b.H_tot - HI;
     if (!u_next && !bad) {
         // interior by runs of 4, border by the general kernel (its border blocks only)
-        k_batch_pack4<<<(HI + BP4_SPAN - 1) / BP4_SPAN, BP_THREADS, 0, s>>>(b, u_origin, u_twin);
+        k_batch_pack4<<<(HI + BP4_SPAN - 1) / BP4_SPAN, BP_THREADS, 0, s>>>(b, u_origin, u_twin, input_err);
         const int32_t nbI = (HI + BP_SPAN - 1) / BP_SPAN, nbB = (HB + BP_SPAN - 1) / BP_SPAN;
-        if (nbB > 0) k_batch_pack<<<nbB, BP_THREADS, 0, s>>>(b, u_origin, u_twin, nullptr, nullptr, nullptr, nbI);
+        if (nbB > 0)
+            k_batch_pack<<<nbB, BP_THREADS, 0, s>>>(b, u_origin, u_twin, nullptr, nullptr, nullptr, input_err, nbI);
         return;
     }
     const int32_t blocks = (HI + BP_SPAN - 1) / BP_SPAN + (HB + BP_SPAN - 1) / BP_SPAN;
-    k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad, 0);
+    k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad, input_err, 0);
 }
 
 void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s) {

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned lon
     w.offsets[P] = (int32_t)NF;
     w.ctrl->n_polygons = P;
     w.ctrl->n_frontier = (int32_t)NF;
+    if (w.input_err && *w.input_err) atomicOr(&w.ctrl->error, DEV_ERR_INPUT);
 }
 
 // ===========================================================================

@@ -277,6 +277,7 @@ static int batch_alloc(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t 
     if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_twin = (int32_t *)p;
     if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.next = (int32_t *)p;
     if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.prev = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t))) == 0) c->w.input_err = (int32_t *)p;
     c->mesh.origin = c->u_origin;
     c->mesh.twin = c->u_twin;
     bv.v_off = d_off[0];
@@ -398,7 +399,8 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
     auto end = [&](int i) -> cudaError_t { return timing ? cudaEventRecord(c->ev_end[i], s) : cudaSuccess; };
     if (c->is_batch) {
         CK(begin(10));
-        launch_batch_pack(c->bv, c->u_origin, c->u_twin, nullptr, nullptr, nullptr, s);
+        CK(cudaMemsetAsync(c->w.input_err, 0, sizeof(int32_t), s));
+        launch_batch_pack(c->bv, c->u_origin, c->u_twin, nullptr, nullptr, nullptr, c->w.input_err, s);
         CK(end(10));
     }
     void (*stages[kCore])(const MeshView &, const Work &, cudaStream_t) = {
@@ -471,6 +473,7 @@ int polylla_release_graph(polylla_ctx *c) {
 }
 
 static int device_status(const DevCtrl &h) {
+    if (h.error & DEV_ERR_INPUT) return POLYLLA_ERR_INVALID_MESH;
     if (h.error & DEV_ERR_NONTERMINATING) return POLYLLA_ERR_NONTERMINATING;
     if (h.error & DEV_ERR_CAPACITY) return POLYLLA_ERR_CAPACITY;
     if (h.error & DEV_ERR_TIMEOUT) return POLYLLA_ERR_TIMEOUT;
@@ -669,7 +672,7 @@ int polylla_batch_create(polylla_ctx **out, const polylla_batch *b, const polyll
             // arrays, then the single-mesh layout check on the union
             cudaError_t e = cudaMemsetAsync(c->d_bad, 0, sizeof(int32_t), s);
             if (e == cudaSuccess) {
-                launch_batch_pack(bv, c->u_origin, c->u_twin, c->mesh.next, c->mesh.prev, c->d_bad, s);
+                launch_batch_pack(bv, c->u_origin, c->u_twin, c->mesh.next, c->mesh.prev, c->d_bad, nullptr, s);
                 e = cudaGetLastError();
             }
             int32_t bad = 0;

@@ -24,6 +24,7 @@ enum : int32_t {
     DEV_ERR_NONTERMINATING = 1,
     DEV_ERR_CAPACITY = 2,
     DEV_ERR_TIMEOUT = 4,
+    DEV_ERR_INPUT = 8,           // a batch mesh held an index out of its range
 };
 
 struct DevCtrl {
@@ -76,6 +77,7 @@ struct Work {
     const int32_t *loc_t_off;    // [loc_n+1] triangle offset of each mesh
     const int32_t *loc_v_off;    // [loc_n+1] vertex offset of each mesh
     int32_t loc_n;               // number of meshes (0: a single mesh)
+    int32_t *input_err;          // batches: set by the pack on an out-of-range index
 };
 
 // A batch of independent meshes, each in the single-mesh layout with its own
@@ -206,7 +208,7 @@ int polygons_configure();
 int emit_blocks_per_sm();
 // batches (kernels_batch.cu)
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
-                       int32_t *bad, cudaStream_t s);
+                       int32_t *bad, int32_t *input_err, cudaStream_t s);
 void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s);
 void launch_batch_ranges(const BatchView &b, const Work &w, int32_t *poly_off, cudaStream_t s);  // two kernels
 void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_off, int32_t *local_offsets,

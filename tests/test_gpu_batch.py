@@ -163,3 +163,21 @@ def test_batch_4096_full_size_matches_oracle():
     db, g = batch_run(meshes, graph=True, tune=True)
     assert_batch_parity(meshes, db, g)
     polylla.polylla_tuning_cache_clear()
+
+
+def test_unvalidated_batch_with_out_of_range_index_reports_invalid_mesh():
+    import torch
+
+    build.build_library()
+    meshes = [meshgen.exact_grid(5), meshgen.random_delaunay(200, seed=4)]
+    db = polylla.DeviceBatch.from_host(meshes)
+    ctx = polylla.polylla_batch_create(db, validate=False)
+    try:
+        db.twin[meshes[0].n_halfedges + 3] = -12345      # a twin of mesh 1, out of range
+        polylla.polylla_generate(ctx)
+        with pytest.raises(polylla.PolyllaError) as e:
+            polylla.polylla_get_polygons(ctx)
+        assert e.value.status == -2
+        torch.cuda.synchronize()
+    finally:
+        polylla.polylla_destroy(ctx)

@@ -112,3 +112,22 @@ def test_served_recipe_pool_matches_oracle():
     assert any(i >= len(small) for i in last), "no large request in the trace"
     for i, info in sorted(last.items()):
         _check(pool[i], info, hrs[i].result(info), oracle.run_mesh(pool[i]), f"pool mesh {i} ({pool[i].name})")
+
+
+def test_malformed_request_fails_cleanly():
+    """Indices outside a request's own mesh are caught by the packing, kept
+    inside the mesh (no access leaves it) and reported as an invalid mesh;
+    the server keeps serving."""
+    build.build_library()
+    good = meshgen.random_delaunay(300, seed=12)
+    bad = meshgen.random_delaunay(300, seed=13)
+    bad.twin = bad.twin.copy()
+    bad.origin = bad.origin.copy()
+    bad.twin[7] = 10 ** 9            # far outside the mesh
+    bad.origin[11] = -5
+    with polylla.Server(memory_budget=1 << 30, n_slots=2) as srv:
+        info = srv.wait(srv.submit(polylla.HostRequest(bad)))
+        assert info["status"] == -2
+        hr = polylla.HostRequest(good)
+        info = srv.wait(srv.submit(hr))
+        _check(good, info, hr.result(info), oracle.run_mesh(good), "after a malformed request")
