@@ -405,6 +405,19 @@ def run_gb300(args):
         e2e = {"value": ws * T / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "polylla_generate_host (pinned host buffers, copies inside the timed region)"}
+        # the same steps as a stream of requests through the serving loop:
+        # one step's copies in overlap another's copies out
+        hr = polylla.HostRequest(mesh)
+        with polylla.Server(memory_budget=SERVE_RECIPE["budget"], n_slots=3) as srv:
+            srv.replay([hr] * 2, [0.0, 0.0])
+            dist_barrier(ws)
+            rc, lat, infos = srv.replay([hr] * e_steps, [0.0] * e_steps)
+            assert rc == 0 and infos[-1]["n_polygons"] == P
+            span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        p_ms = dist_max(1e3 * span / e_steps, ws)
+        e2e["pipelined"] = {"value": ws * T / (p_ms * 1e-3), "unit": UNIT, "ms_per_step": p_ms,
+                            "api": f"polylla_server_replay of {e_steps} requests of the mesh, all arriving at once"}
+        del hr
 
     # ---- CPU baseline: the oracle, bounded sample, rank 0, N = 1 only -----
     cpu = None

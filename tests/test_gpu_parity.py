@@ -79,6 +79,29 @@ def test_parity_with_barrier_tips(mesh):
     assert_parity(mesh, g, r)
 
 
+def test_parity_random_sweep():
+    """Forty small meshes of random kinds and sizes (3-point to 600-point
+    Delaunay meshes, 2x2 to 41x41 perturbed and exact grids, lattice meshes
+    with exact ties), every array against the oracle."""
+    rng = np.random.default_rng(2024)
+    for i in range(40):
+        kind = i % 4
+        if kind == 0:
+            mesh = meshgen.random_delaunay(int(rng.integers(3, 600)), seed=int(rng.integers(1 << 30)))
+        elif kind == 1:
+            mesh = meshgen.perturbed_grid(int(rng.integers(2, 42)), 0.3, seed=int(rng.integers(1 << 30)))
+        elif kind == 2:
+            mesh = meshgen.exact_grid(int(rng.integers(2, 42)))
+        else:
+            try:
+                mesh = meshgen.lattice_delaunay(int(rng.integers(10, 300)), int(rng.integers(8, 30)),
+                                                seed=int(rng.integers(1 << 30)))
+            except ValueError:
+                continue
+        g = gpu_run(mesh)
+        assert_parity(mesh, g, oracle.run_mesh(mesh))
+
+
 def test_parity_generate_is_repeatable():
     """generate never reads the input next/prev of interior half-edges, so a
     second and third call on the rewritten arrays give the same result."""
