@@ -4,14 +4,19 @@
 // generate; nothing is allocated on the hot path):
 //   le      [T]   uint8  local index of each triangle's longest half-edge
 //   flags   [T]   uint8  bits 0-2 F1 (frontier after repair) of 3t+k,
+//                        bits 3-5 walk-start marks (next and prev larger),
 //                        bit 6 the triangle's longest half-edge is a seed
 //   tips    [V]   int32  F0 half-edge leaving each barrier tip
 //   chords  [V]   int32  chord half-edge leaving each barrier tip
 //   cand  [3T]    int32  walk starts (marked frontier half-edges), ascending
 //   res   [3T]    int32  polygon length of each start that is a minimum, else 0
-//   blk_a/blk_a_pre, blk_b/blk_b_pre  u64  block and chunk totals, scanned
+//   blk_a/blk_a_pre   u64  start counts per CC_TRI triangles, scanned
+//   blk_b/blk_b_pre   u64  (polygons, length) per CHUNK starts, scanned
+//   grp   [3T/32] u64    (polygons, length) per 32 starts
 //   seeds [T], offsets [T+1], he_list [3T], v_list [3T]   CSR output
 //   ctrl          DevCtrl       counters and the device error word
+// A batch context adds the union origin/twin/next/prev [H], the per-mesh
+// prefix sums and polygon ranges, and the input-check word.
 #pragma once
 
 #include <cstdint>
@@ -99,8 +104,9 @@ struct BatchView {
 };
 
 // output kernels: start counting/compaction over blocks of CC_TRI
-// triangles (16 per thread, one int4 of flags), walks and emission over
-// chunks of CHUNK starts, single-block scans of the block/chunk totals
+// triangles (16 per thread, one int4 of flags), walks and emission per warp
+// over groups of 32 and 64 starts inside chunks of CHUNK starts,
+// single-block scans of the block and chunk totals
 constexpr int CC_THREADS = 1024;
 constexpr int CC_PER = 16;
 constexpr int CC_TRI = CC_THREADS * CC_PER;
