@@ -238,7 +238,9 @@ def algorithmic_bytes(T, V, NF, P):
 # reference arm: the CPU oracle as it stands
 # ---------------------------------------------------------------------------
 
-def ref_sample_mesh(workload: str):
+def ref_sample_mesh(workload: str, runs: int = 3):
+    """A bounded sample of the workload for the oracle: about 10-30 s of
+    single-threaded CPU work over ``runs`` runs on the GPU machine's cores."""
     from paper_2403_14723_gb300 import meshgen
 
     if workload == "served":
@@ -257,7 +259,11 @@ def ref_sample_mesh(workload: str):
         return ms, f"the first {len(ms)} meshes of the batch ({sum(m.n_triangles for m in ms):,} triangles)"
 
     if workload.startswith("pgrid_"):
-        return meshgen.perturbed_grid(2048, 0.3, seed=3), "perturbed grid 2048x2048 (8,380,418 triangles), same recipe"
+        # about 60 ns per triangle on one Grace core: 2048^2 for a few runs,
+        # smaller grids of the same recipe for many
+        side = 2048 if runs <= 40 else (1024 if runs <= 160 else 512)
+        m = meshgen.perturbed_grid(side, 0.3, seed=3)
+        return m, f"perturbed grid {side}x{side} ({m.n_triangles:,} triangles), same recipe"
     if workload == "delaunay_1m":
         return meshgen.random_delaunay(1_000_000, seed=2), "the full 1M-point Delaunay mesh"
     return meshgen.workload(workload), f"the full {workload} mesh"
@@ -269,7 +275,7 @@ def run_reference(args):
         return 0
     import oracle
 
-    mesh, sample = ref_sample_mesh(args.workload)
+    mesh, sample = ref_sample_mesh(args.workload, runs=args.steps + args.warmup)
     meshes = mesh if isinstance(mesh, list) else [mesh]
     n_tri = sum(m.n_triangles for m in meshes)
     oracle.build()
