@@ -72,6 +72,13 @@ def _bind(lib):
         i32p, i32p, i32p, i32p,
         i64p, f64p,
     ]
+    lib.oracle_lepp.restype = ctypes.c_int
+    lib.oracle_lepp.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int32)]
+    lib.oracle_lepp_path.restype = ctypes.c_int32
+    lib.oracle_lepp_path.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8),
+                                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
     lib.oracle_stats_count.restype = ctypes.c_int
     assert lib.oracle_stats_count() == len(STAT_NAMES)
     return lib
@@ -174,6 +181,37 @@ def run(coords, origin, twin, next, prev, n_triangles: int, lib=None) -> OracleR
         he_list=he_list[:NF].copy(), v_list=v_list[:NF].copy(),
         stats=st, times={n: float(v) for n, v in zip(TIME_NAMES, times)},
     )
+
+
+def lepp(mesh, longest: np.ndarray, lib=None):
+    """Lepp of every triangle (Definition 1) from the label phase's longest
+    edges: ``(terminal [T], length [T])``, terminal = the seed half-edge of
+    the terminal edge the path ends on, length = triangles in the path."""
+    lib = lib if lib is not None else _load()
+    T = int(mesh.n_triangles)
+    twin = np.ascontiguousarray(mesh.twin, dtype=np.int32)
+    lg = np.ascontiguousarray(longest, dtype=np.uint8)
+    term = np.zeros(max(T, 1), np.int32)
+    length = np.zeros(max(T, 1), np.int32)
+    rc = lib.oracle_lepp(T, int(twin.shape[0]), _ptr(twin, ctypes.c_int32), _ptr(lg, ctypes.c_uint8),
+                         _ptr(term, ctypes.c_int32), _ptr(length, ctypes.c_int32))
+    if rc != 0:
+        raise RuntimeError(f"oracle failed: {ERRORS.get(rc, rc)}")
+    return term[:T].copy(), length[:T].copy()
+
+
+def lepp_path(mesh, longest: np.ndarray, t0: int, lib=None) -> np.ndarray:
+    """The triangles of Lepp(t0), in order."""
+    lib = lib if lib is not None else _load()
+    twin = np.ascontiguousarray(mesh.twin, dtype=np.int32)
+    lg = np.ascontiguousarray(longest, dtype=np.uint8)
+    cap = int(mesh.n_triangles) + 1
+    path = np.zeros(cap, np.int32)
+    n = lib.oracle_lepp_path(int(mesh.n_triangles), _ptr(twin, ctypes.c_int32), _ptr(lg, ctypes.c_uint8), int(t0),
+                             _ptr(path, ctypes.c_int32), cap)
+    if n < 0:
+        raise RuntimeError("oracle Lepp path longer than the mesh")
+    return path[:n].copy()
 
 
 def run_mesh(mesh, lib=None) -> OracleResult:

@@ -15,6 +15,10 @@
  *   Repair phase     Algorithm 6                              -- Section 5.3
  *   Output           every polygon listed from its smallest half-edge,
  *                    polygons in ascending order of that half-edge.
+ *   Lepp             oracle_lepp: the longest-edge propagation path of
+ *                    every triangle (Definition 1, Section 3.1) from the
+ *                    longest edges of the label phase -- Section 1 lists
+ *                    it as a reusable data-parallel building block.
  *
  * Half-edge queries follow Section 4 ("Half-edge representation" and its
  * CUDA subsection), with the garbled formulas read as:
@@ -381,4 +385,68 @@ done:
     free(tips_start);
     free(subseeds);
     return status;
+}
+
+/*
+ * Lepp (Definition 1): Lepp(t0) is t0, t1, ..., where t_i is the neighbour
+ * of t_{i-1} across the longest edge of t_{i-1}; it ends at the terminal
+ * edge, the longest edge shared by the last two triangles (both have it as
+ * their longest edge), or at a longest edge on the border.  Reading (the
+ * definition's indices are garbled): the path lists every triangle met,
+ * the last two triangles of an interior terminal edge included, so its
+ * length is 1 for a triangle whose longest edge is a border edge.
+ *
+ * For every triangle t: terminal[t] = the seed half-edge of the terminal
+ * edge (reading R4: the smaller half of an interior terminal edge, the
+ * interior half of a border one), length[t] = number of triangles in
+ * Lepp(t).  longest[H] is the label phase's longest-edge flag per
+ * half-edge.  Returns OR_OK, or OR_ERR_NONTERMINATING when a path exceeds T
+ * triangles (impossible under reading R1's strict order).
+ */
+int oracle_lepp(int32_t T, int32_t H, const int32_t *twin, const uint8_t *longest,
+                int32_t *terminal, int32_t *length) {
+    const int32_t HI = 3 * T;
+    (void)H;
+    for (int32_t t0 = 0; t0 < T; t0++) {
+        int32_t t = t0, n = 1;
+        for (;;) {
+            int32_t e = 3 * t;               /* the longest half-edge of t */
+            while (!longest[e]) e++;
+            const int32_t tw = twin[e];
+            if (tw >= HI) {                  /* border: e is a border-terminal edge */
+                terminal[t0] = e;
+                break;
+            }
+            const int32_t t1 = tw / 3;       /* the neighbour across it */
+            n++;
+            if (longest[tw]) {               /* shared longest edge: terminal */
+                terminal[t0] = e < tw ? e : tw;
+                break;
+            }
+            t = t1;
+            if (n > T + 1) return OR_ERR_NONTERMINATING;
+        }
+        length[t0] = n;
+    }
+    return OR_OK;
+}
+
+/* The path itself: the triangles of Lepp(t0) in order into path (capacity
+ * cap); returns its length, or -1 when cap is too small. */
+int32_t oracle_lepp_path(int32_t T, const int32_t *twin, const uint8_t *longest, int32_t t0,
+                         int32_t *path, int32_t cap) {
+    const int32_t HI = 3 * T;
+    int32_t t = t0, n = 0;
+    if (n >= cap) return -1;
+    path[n++] = t;
+    for (;;) {
+        int32_t e = 3 * t;
+        while (!longest[e]) e++;
+        const int32_t tw = twin[e];
+        if (tw >= HI) return n;
+        if (n >= cap) return -1;
+        path[n++] = tw / 3;
+        if (longest[tw]) return n;
+        t = tw / 3;
+    }
 }
