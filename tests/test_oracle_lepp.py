@@ -26,8 +26,12 @@ def _meshes():
 
 @pytest.mark.parametrize("mesh", _meshes(), ids=lambda m: m.name)
 def test_lepp_terminal_matches_brute_force(mesh):
-    r = oracle.run_mesh(mesh)
-    term, length = oracle.lepp(mesh, r.longest)
+    pin_lepp_terminal(mesh)
+
+
+def pin_lepp_terminal(mesh, lib=None):
+    r = oracle.run_mesh(mesh, lib=lib)
+    term, length = oracle.lepp(mesh, r.longest, lib=lib)
     le_bf = checks.brute_force_longest(mesh)
     assert np.array_equal(term, checks.lepp_terminal(mesh, le_bf))
     # regions grouped by terminal edge are the components over non-frontier edges
@@ -38,13 +42,17 @@ def test_lepp_terminal_matches_brute_force(mesh):
 
 @pytest.mark.parametrize("mesh", _meshes(), ids=lambda m: m.name)
 def test_lepp_length_recursion_and_paths(mesh):
+    pin_lepp_recursion(mesh)
+
+
+def pin_lepp_recursion(mesh, lib=None):
     """length(t) is 1 on a border longest edge, 2 on a terminal edge, else
     1 + length of the neighbour across the longest edge; every path steps
     across the previous triangle's longest edge and ends on the terminal."""
-    r = oracle.run_mesh(mesh)
+    r = oracle.run_mesh(mesh, lib=lib)
     T = mesh.n_triangles
     HI = 3 * T
-    term, length = oracle.lepp(mesh, r.longest)
+    term, length = oracle.lepp(mesh, r.longest, lib=lib)
     le = checks.brute_force_longest(mesh)
     for t in range(T):
         e = 3 * t + int(le[t])
@@ -58,7 +66,7 @@ def test_lepp_length_recursion_and_paths(mesh):
         else:
             assert length[t] == 1 + length[n] and term[t] == term[n]
     for t in range(0, T, max(1, T // 25)):
-        path = oracle.lepp_path(mesh, r.longest, t)
+        path = oracle.lepp_path(mesh, r.longest, t, lib=lib)
         assert len(path) == length[t] and path[0] == t
         for a, b in zip(path[:-1], path[1:]):
             e = 3 * a + int(le[a])
@@ -67,12 +75,16 @@ def test_lepp_length_recursion_and_paths(mesh):
 
 @pytest.mark.parametrize("s", [2, 5, 9])
 def test_lepp_exact_grid_closed_form(s):
+    pin_lepp_grid(s)
+
+
+def pin_lepp_grid(s, lib=None):
     """Algorithm 15's grid: every cell's diagonal is the longest edge of both
     its triangles, so every Lepp is the cell's two triangles and ends on the
     diagonal."""
     m = meshgen.exact_grid(s)
-    r = oracle.run_mesh(m)
-    term, length = oracle.lepp(m, r.longest)
+    r = oracle.run_mesh(m, lib=lib)
+    term, length = oracle.lepp(m, r.longest, lib=lib)
     assert np.all(length == 2)
     assert len(set(term.tolist())) == (s - 1) ** 2
     for t in range(m.n_triangles):

@@ -5,7 +5,9 @@ Each case compiles a copy of the oracle source with one planted mistake
 of ``test_oracle_pins`` fails on it.  The mistakes are the kind a reader of
 the paper could make: a dropped term, a reversed rotation, an off-by-one
 rotation count, the frontier condition as printed in Algorithm 3, a wrong
-tie-break, a missing seed rule, output not started at the polygon minimum.
+tie-break, a missing seed rule, output not started at the polygon minimum,
+and, for the Lepp, the wrong half of a terminal edge or a path that stops
+before the terminal edge's second triangle.
 """
 import os
 import shutil
@@ -15,6 +17,7 @@ import pytest
 
 import oracle
 from paper_2403_14723_gb300 import meshgen
+from tests import test_oracle_lepp as lepp_pins
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "polylla_oracle.c")
@@ -37,6 +40,12 @@ MUTANTS = {
                        "            (void)tw;"),
     "output_from_next": ("        int32_t cur = e;\n        int64_t len = 0;",
                          "        int32_t cur = next_out[e];\n        int64_t len = 0;"),
+    "lepp_terminal_larger_half": ("                terminal[t0] = e < tw ? e : tw;",
+                                  "                terminal[t0] = e < tw ? tw : e;"),
+    "lepp_border_half": ("                terminal[t0] = e;\n                break;",
+                         "                terminal[t0] = tw;\n                break;"),
+    "lepp_path_stops_before_terminal": ("        path[n++] = tw / 3;\n        if (longest[tw]) return n;",
+                                        "        if (longest[tw]) return n;\n        path[n++] = tw / 3;"),
 }
 
 
@@ -64,6 +73,9 @@ def _pins_hold(lib) -> bool:
         lambda: pins.pin_tips(_tip_mesh(), lib),
         lambda: pins.pin_invariants(meshgen.random_delaunay(500, seed=300), lib),
         lambda: pins.pin_relabelling(7, lib),
+        lambda: lepp_pins.pin_lepp_terminal(meshgen.random_delaunay(130, seed=301), lib),
+        lambda: lepp_pins.pin_lepp_recursion(meshgen.random_delaunay(200, seed=302), lib),
+        lambda: lepp_pins.pin_lepp_grid(5, lib),
     ]
     for c in cases:
         try:
