@@ -25,6 +25,7 @@ time over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -382,6 +383,28 @@ def run_gb300(args):
                        "frac": total_alg / (ms * 1e-3) / 1e9 / peak},
     }
 
+    # ---- the Lepp primitive over the same mesh (after a generate) ---------
+    term_buf = torch.empty(T, dtype=torch.int32, device=dev)
+    len_buf = torch.empty(T, dtype=torch.int32, device=dev)
+    polylla.polylla_generate(ctx, stream)
+    lib.polylla_lepp_terminal(ctypes.c_void_p(ctx), ctypes.c_void_p(term_buf.data_ptr()),
+                              ctypes.c_void_p(len_buf.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    l_steps = max(3, min(args.steps, 50))
+    ls = [torch.cuda.Event(enable_timing=True) for _ in range(l_steps)]
+    le_ = [torch.cuda.Event(enable_timing=True) for _ in range(l_steps)]
+    for i in range(l_steps):
+        flush.fill_(i)
+        ls[i].record(stream)
+        lib.polylla_lepp_terminal(ctypes.c_void_p(ctx), ctypes.c_void_p(term_buf.data_ptr()),
+                                  ctypes.c_void_p(len_buf.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        le_[i].record(stream)
+    torch.cuda.synchronize()
+    lepp_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ls, le_))
+    lepp_mean = float(len_buf.double().mean())
+    lepp = {"ms": lepp_ms, "triangles_per_s": T / (lepp_ms * 1e-3), "mean_path_triangles": lepp_mean,
+            "api": "polylla_lepp_terminal: terminal seed and path length of every triangle"}
+    del term_buf, len_buf
+
     # ---- end to end through the host-buffer entry point ------------------
     e2e = None
     if not args.no_e2e:
@@ -451,7 +474,7 @@ def run_gb300(args):
                        "polygons": P, "frontier_halfedges": NF, "parallelism": f"replicas x{ws}",
                        "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
                              f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "lepp": lepp,
             "gpu_launches": launches, "clocks": clocks,
             "kernel_digest": kernel_digest(), "core_kernel_digest": core_kernel_digest(),
         }
@@ -644,7 +667,7 @@ def run_batched(args):
                                    "launches_per_step": 10 * n_meshes,
                                    "how": "polylla_generate per mesh, back to back on one stream"},
             "without_graph": {"value": ws * T / (ms_nograph * 1e-3), "unit": UNIT, "ms_per_step": ms_nograph},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "lepp": lepp,
             "gpu_launches": launches, "clocks": clocks, "kernel_digest": kernel_digest(),
         }
         print(json.dumps(line), flush=True)

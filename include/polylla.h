@@ -300,6 +300,34 @@ int polylla_autotune(polylla_ctx *ctx, int32_t reps, polylla_tuning *out, polyll
 int polylla_tuning_cache_clear(void);
 
 /*
+ * Longest-edge propagation paths (Definition 1, Section 3.1; Section 1
+ * lists a data-parallel Lepp among the paper's contributions, as a building
+ * block for Lepp-based refinement).  Lepp(t0) = t0, t1, ...: t_i is the
+ * neighbour of t_{i-1} across the longest edge of t_{i-1}; the path ends at
+ * the terminal edge, the longest edge of both of its triangles (both are
+ * listed), or at a longest edge on the border.  Both calls use the longest
+ * edges of the context's last generate (so they follow it on the same
+ * stream), are asynchronous, and report a device error (NONTERMINATING,
+ * CAPACITY, INVALID_MESH for a query outside [0, T)) through
+ * polylla_last_error until the next generate.  Single-mesh contexts only
+ * (INVALID_ARGUMENT on a batch).
+ *
+ * polylla_lepp_terminal: for every triangle t, terminal[t] = the seed
+ *   half-edge of the terminal edge its Lepp ends on -- the smaller half of
+ *   an interior terminal edge, the interior half of a border one -- which
+ *   names t's terminal-edge region (Definition 2); length[t] (may be NULL)
+ *   = the number of triangles in Lepp(t).  Device arrays of T int32.
+ * polylla_lepp_paths: the paths of n query triangles tri[0..n) (device,
+ *   1 <= n <= T): offsets[n+1] (device) gets the exclusive prefix of the
+ *   path lengths, offsets[n] the total, and paths[capacity] (device) the
+ *   triangles of every path in query order; past the capacity paths are
+ *   cut and CAPACITY is reported.
+ */
+int polylla_lepp_terminal(polylla_ctx *ctx, int32_t *terminal, int32_t *length, polylla_stream stream);
+int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t *offsets, int32_t *paths,
+                       int64_t capacity, polylla_stream stream);
+
+/*
  * Serving (no counterpart in the paper): a request loop with continuous
  * batching.  Requests are meshes in host memory (pinned for full copy
  * speed); a scheduler thread owned by the server admits them, in arrival

@@ -361,6 +361,11 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
     }
 }
 
+void launch_scan_u64(const unsigned long long *in, unsigned long long *out, int32_t n, unsigned long long *grand,
+                     cudaStream_t s) {
+    k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, 0, grand, MeshView{}, Work{}, 0);
+}
+
 int polygons_configure() { return 0; }
 
 int emit_blocks_per_sm() {

@@ -44,6 +44,8 @@ struct polylla_ctx {
     BatchView bv{};
     int32_t *poly_off = nullptr;    // [n+1] first polygon of each mesh
     int32_t *u_origin = nullptr, *u_twin = nullptr;  // union arrays, owned
+    // Lepp paths: per-1024-query totals, their scan, the grand total
+    unsigned long long *lepp_blk = nullptr, *lepp_blk_pre = nullptr, *lepp_total = nullptr;
     // serving: per-mesh metadata and rebased offsets after each run
     bool serve = false;
     int32_t *meta = nullptr;           // [4 n_cap]
@@ -225,6 +227,13 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.v_list = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(DevCtrl)))) return rc;
     c->w.ctrl = (DevCtrl *)p;
+    const size_t n_lepp_blk = ((size_t)T + 1023) / 1024 + 1;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * n_lepp_blk))) return rc;
+    c->lepp_blk = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * n_lepp_blk))) return rc;
+    c->lepp_blk_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long)))) return rc;
+    c->lepp_total = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t)))) return rc;
     c->d_bad = (int32_t *)p;
     cudaError_t e = cudaMallocHost((void **)&c->h_ctrl, sizeof(DevCtrl));
@@ -790,6 +799,30 @@ int polylla_tuning_cache_clear(void) {
     std::lock_guard<std::mutex> g(g_tune_lock);
     for (int d = 0; d < kTuneDevices; d++)
         for (int b = 0; b < kTuneBuckets; b++) g_tune[d][b].set = false;
+    return POLYLLA_OK;
+}
+
+// ---- Lepp ------------------------------------------------------------------------
+
+int polylla_lepp_terminal(polylla_ctx *c, int32_t *terminal, int32_t *length, polylla_stream stream) {
+    if (!c || !terminal || c->is_batch || c->serve) return POLYLLA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    launch_lepp_terminal(c->mesh, c->w, terminal, length, &c->w.ctrl->error, s);
+    CK(cudaGetLastError());
+    return POLYLLA_OK;
+}
+
+int polylla_lepp_paths(polylla_ctx *c, const int32_t *tri, int32_t n, int32_t *offsets, int32_t *paths,
+                       int64_t capacity, polylla_stream stream) {
+    if (!c || !tri || !offsets || (!paths && capacity > 0) || capacity < 0 || c->is_batch || c->serve)
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    if (n < 1 || n > c->mesh.T) return POLYLLA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    launch_lepp_paths(c->mesh, c->w, tri, n, offsets, paths, capacity, c->lepp_blk, c->lepp_blk_pre, c->lepp_total,
+                      &c->w.ctrl->error, s);
+    CK(cudaGetLastError());
     return POLYLLA_OK;
 }
 

@@ -212,6 +212,15 @@ void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_emit(const MeshView &m, const Work &w, cudaStream_t s);
 int polygons_configure();
 int emit_blocks_per_sm();
+// exclusive scan of n u64 values by one block; *grand gets the sum
+void launch_scan_u64(const unsigned long long *in, unsigned long long *out, int32_t n, unsigned long long *grand,
+                     cudaStream_t s);
+// Lepp (kernels_lepp.cu)
+void launch_lepp_terminal(const MeshView &m, const Work &w, int32_t *terminal, int32_t *length, int32_t *err,
+                          cudaStream_t s);
+void launch_lepp_paths(const MeshView &m, const Work &w, const int32_t *tri, int32_t n, int32_t *offsets,
+                       int32_t *paths, int64_t capacity, unsigned long long *blk, unsigned long long *blk_pre,
+                       unsigned long long *total, int32_t *err, cudaStream_t s);
 // batches (kernels_batch.cu)
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
                        int32_t *bad, int32_t *input_err, cudaStream_t s);

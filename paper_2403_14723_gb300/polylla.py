@@ -140,6 +140,9 @@ _SIGNATURES = {
     "polylla_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(polylla_tuning),
                                         ctypes.c_void_p]),
     "polylla_tuning_cache_clear": (ctypes.c_int, []),
+    "polylla_lepp_terminal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polylla_lepp_paths": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "polylla_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_server_options)]),
     "polylla_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_request),
                                              ctypes.POINTER(ctypes.c_int64)]),
@@ -480,6 +483,34 @@ def polylla_batch_polygon_offsets(ctx: int, n_meshes: int):
     _check(load_library().polylla_batch_polygon_offsets(ctypes.c_void_p(ctx), ctypes.byref(p)),
            "polylla_batch_polygon_offsets")
     return _view(p.value, n_meshes + 1, "<i4", torch.int32)
+
+
+def polylla_lepp_terminal(ctx: int, n_triangles: int, with_length: bool = True, stream=None):
+    """Lepp terminal seed (and path length) of every triangle, after a
+    generate: device int32 tensors ``(terminal, length or None)``."""
+    import torch
+
+    term = torch.empty(n_triangles, dtype=torch.int32, device="cuda")
+    length = torch.empty(n_triangles, dtype=torch.int32, device="cuda") if with_length else None
+    _check(load_library().polylla_lepp_terminal(
+        ctypes.c_void_p(ctx), ctypes.c_void_p(term.data_ptr()),
+        ctypes.c_void_p(length.data_ptr()) if length is not None else None, _stream_ptr(stream)),
+        "polylla_lepp_terminal")
+    return term, length
+
+
+def polylla_lepp_paths(ctx: int, tri, capacity: int, stream=None):
+    """Lepp paths of the query triangles ``tri`` (device int32 tensor):
+    ``(offsets [n+1], paths [capacity])`` device int32 tensors."""
+    import torch
+
+    n = tri.numel()
+    offsets = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    paths = torch.empty(max(int(capacity), 1), dtype=torch.int32, device="cuda")
+    _check(load_library().polylla_lepp_paths(
+        ctypes.c_void_p(ctx), _dev_ptr(tri, torch.int32, n), int(n), ctypes.c_void_p(offsets.data_ptr()),
+        ctypes.c_void_p(paths.data_ptr()), int(capacity), _stream_ptr(stream)), "polylla_lepp_paths")
+    return offsets, paths
 
 
 class HostRequest:
