@@ -63,7 +63,9 @@ typedef struct {
 } polylla_mesh;
 
 typedef struct {
-    int32_t validate;      /* nonzero: check the mesh layout at create (default on) */
+    int32_t validate;      /* nonzero: check the mesh layout at create (default on);
+                              with 0 the caller guarantees the layout: the
+                              kernels index with the input values unchecked */
     int32_t max_rotation;  /* cap on one vertex rotation (0: 4096)               */
 } polylla_options;
 
