@@ -328,6 +328,8 @@ def run_gb300(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     ctx = polylla.polylla_create(dm, stream=stream)
     lib = polylla.load_library()
+    # launch settings picked by the library's autotuner on this mesh
+    tuning = polylla.polylla_autotune(ctx, reps=5, stream=stream)
 
     def step():
         polylla.polylla_generate(ctx, stream)
@@ -472,6 +474,7 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f64/int32", "data": "synthetic",
             "config": {"workload": args.workload, "triangles": T, "vertices": V, "halfedges": H,
                        "polygons": P, "frontier_halfedges": NF, "parallelism": f"replicas x{ws}",
+                       "tuning": tuning,
                        "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
                              f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "lepp": lepp,
