@@ -338,24 +338,20 @@ __global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
             if (((fl >> k) & 1u) && ((fl >> j) & 1u)) s_pv[lb + j] = e0 + k;  // successor in the same triangle
         }
     }
-    // compact the warp's pending rotations
-    const uint32_t cnt = __popc(pend);
-    uint32_t incl = cnt;
+    // compact the warp's pending rotations, local edge by local edge (the
+    // order of the tasks does not matter: each writes its own slots)
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t total = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    uint32_t slot = incl - cnt;
-    if (pend) {
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if ((pend >> k) & 1u) {
-                const int j = k == 2 ? 0 : k + 1;
-                s_task[wid][slot++] = make_int4(e0 + k, tw[k], ttri[j], (int32_t)(tloc[j] | (lnb[j] << 2)));
-            }
+    for (int k = 0; k < 3; k++) {
+        const bool mine = (pend >> k) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+        if (mine) {
+            const int j = k == 2 ? 0 : k + 1;
+            s_task[wid][total + __popc(bal & below)] =
+                make_int4(e0 + k, tw[k], ttri[j], (int32_t)(tloc[j] | (lnb[j] << 2)));
         }
+        total += __popc(bal);
     }
     __syncwarp();
     for (uint32_t i = lane; i < total; i += 32) {
