@@ -676,7 +676,7 @@ def run_batched(args):
                                    "launches_per_step": 10 * n_meshes,
                                    "how": "polylla_generate per mesh, back to back on one stream"},
             "without_graph": {"value": ws * T / (ms_nograph * 1e-3), "unit": UNIT, "ms_per_step": ms_nograph},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "lepp": lepp,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "kernel_digest": kernel_digest(),
         }
         print(json.dumps(line), flush=True)
