@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch settings (profiling runs: no tuning launches before the steps)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served request trace (served workload)")
     ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
@@ -332,7 +334,10 @@ def run_gb300(args):
     ctx = polylla.polylla_create(dm, stream=stream)
     lib = polylla.load_library()
     # launch settings picked by the library's autotuner on this mesh
-    tuning = polylla.polylla_autotune(ctx, reps=5, stream=stream)
+    if args.no_autotune:
+        tuning = polylla.polylla_get_tuning(ctx)
+    else:
+        tuning = polylla.polylla_autotune(ctx, reps=5, stream=stream)
     # the whole generate as one CUDA graph launch per step
     polylla.polylla_capture_graph(ctx, stream)
 
