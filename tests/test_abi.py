@@ -95,3 +95,9 @@ def test_null_arguments_rejected_without_gpu(lib_path):
 
 def test_built_for_sm_103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the built library every call raises."""
+    with pytest.raises(RuntimeError, match="not built"):
+        polylla.load_library(str(tmp_path / "libpolylla_missing.so"))
