@@ -389,6 +389,9 @@ typedef struct {
     double mean_in_ms;           /* per batch, on its stream: copies in,           */
     double mean_run_ms;          /*   kernels and metadata readback,               */
     double mean_out_ms;          /*   from metadata landed to results out          */
+    double max_batch_ms;         /* the slowest batch (in + run + out on its stream) */
+    int64_t max_batch_triangles; /*   its triangles                                */
+    int32_t max_batch_requests;  /*   and requests                                 */
 } polylla_server_stats;
 
 /* Create a server on the current device (allocates all slots; starts the

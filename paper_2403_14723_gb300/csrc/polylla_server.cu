@@ -98,6 +98,9 @@ struct polylla_server {
     int64_t batches = 0, done_count = 0, timed_batches = 0;
     double busy = 0.0;
     double t_in = 0, t_run = 0, t_out = 0;  // summed ms: copies in, kernels + metadata, results out
+    double slowest_ms = 0;                  // the slowest batch on its stream, and its size
+    int64_t slowest_tri = 0;
+    int32_t slowest_n = 0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void loop();
@@ -274,11 +277,18 @@ void polylla_server::loop() {
                         if (cudaEventElapsedTime(&a, s.ev_t0, s.ev_in) == cudaSuccess &&
                             cudaEventElapsedTime(&b, s.ev_in, s.ev_tm) == cudaSuccess &&
                             cudaEventElapsedTime(&c, s.ev_tm, s.ev_to) == cudaSuccess) {
+                            int64_t tri = 0;
+                            for (Req *r : s.reqs) tri += r->r.n_triangles;
                             std::lock_guard<std::mutex> g(mu);
                             t_in += a;
                             t_run += b;
                             t_out += c;
                             timed_batches++;
+                            if (a + b + c > slowest_ms) {
+                                slowest_ms = a + b + c;
+                                slowest_tri = tri;
+                                slowest_n = (int32_t)s.reqs.size();
+                            }
                         }
                     }
                     for (Req *r : s.reqs) {
@@ -503,6 +513,9 @@ int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out) {
     out->mean_in_ms = srv->t_in / nb;
     out->mean_run_ms = srv->t_run / nb;
     out->mean_out_ms = srv->t_out / nb;
+    out->max_batch_ms = srv->slowest_ms;
+    out->max_batch_triangles = srv->slowest_tri;
+    out->max_batch_requests = srv->slowest_n;
     return POLYLLA_OK;
 }
 

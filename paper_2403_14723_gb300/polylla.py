@@ -104,7 +104,9 @@ class polylla_request_info(ctypes.Structure):
 class polylla_server_stats(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("slot_triangles", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("requests_done", ctypes.c_int64), ("busy_seconds", ctypes.c_double),
-                ("mean_in_ms", ctypes.c_double), ("mean_run_ms", ctypes.c_double), ("mean_out_ms", ctypes.c_double)]
+                ("mean_in_ms", ctypes.c_double), ("mean_run_ms", ctypes.c_double), ("mean_out_ms", ctypes.c_double),
+                ("max_batch_ms", ctypes.c_double), ("max_batch_triangles", ctypes.c_int64),
+                ("max_batch_requests", ctypes.c_int32)]
 
 
 # every function the header declares, with its ctypes signature
