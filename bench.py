@@ -284,14 +284,23 @@ def run_reference(args):
     oracle.build()
     times = []
     n_poly = 0
+    stage_s = {}
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        n_poly = sum(oracle.run_mesh(m).n_polygons for m in meshes)
+        rs = [oracle.run_mesh(m) for m in meshes]
         dt = time.perf_counter() - t0
+        n_poly = sum(r.n_polygons for r in rs)
         if i >= args.warmup:
             times.append(dt)
+            for r in rs:
+                for k, v in r.times.items():
+                    stage_s[k] = stage_s.get(k, 0.0) + v
     tot = sum(times)
     value = n_tri * len(times) / tot
+    import platform
+
+    host = {"machine": platform.machine(), "cores": os.cpu_count(), "threads_used": 1,
+            "stage_ms_per_step": {k: 1e3 * v / len(times) for k, v in stage_s.items()}}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
@@ -300,8 +309,10 @@ def run_reference(args):
         "config": {"workload": args.workload, "sample": sample, "triangles": n_tri,
                    "polygons": n_poly},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{sample}; single-threaded sequential oracle, {len(times)} timed runs"},
+                         "sample": f"{sample}; single-threaded sequential oracle (1 of {os.cpu_count()} "
+                                   f"host cores), {len(times)} timed runs"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "host": host,
     }
     print(json.dumps(line), flush=True)
     return 0
