@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--serve-baseline-seconds", type=float, default=10.0,
                     help="trace length replayed through the one-mesh-at-a-time server")
     ap.add_argument("--serve-slots", type=int, default=3, help="batches in flight (served workload)")
+    ap.add_argument("--serve-lane", type=int, default=0,
+                    help="largest request of the server's low-latency lane (0: default, negative: no lane)")
     ap.add_argument("--serve-batch-triangles", type=int, default=0,
                     help="triangles at which a served batch stops growing (0: slot capacity)")
     return ap.parse_args()
@@ -745,6 +747,34 @@ def serve_trace(seconds: float, n_small: int, n_large: int, seed: int):
     return t, pick
 
 
+def batch_trace(log):
+    """Where the served batches' time went: percentiles of each segment of
+    the server's batch log, and the slowest batches in full."""
+    import numpy as np
+
+    if not log:
+        return None
+    seg = {
+        "host_enqueue_ms": [1e3 * (b["t_enqueued"] - b["t_form"]) for b in log],
+        "in_ms": [b["in_ms"] for b in log], "run_ms": [b["run_ms"] for b in log],
+        "idle_ms": [b["idle_ms"] for b in log], "out_ms": [b["out_ms"] for b in log],
+        "host_meta_wait_ms": [1e3 * (b["t_meta_seen"] - b["t_enqueued"]) for b in log],
+        "host_out_wait_ms": [1e3 * (b["t_done"] - b["t_out_enqueued"]) for b in log],
+        "total_ms": [1e3 * (b["t_done"] - b["t_form"]) for b in log],
+    }
+    out = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "max": float(np.max(v))}
+           for k, v in seg.items()}
+    slow = sorted(log, key=lambda b: b["t_done"] - b["t_form"])[-5:]
+    out["batches"] = len(log)
+    out["lane_batches"] = sum(1 for b in log if b["lane"])
+    out["slowest"] = [{"total_ms": round(1e3 * (b["t_done"] - b["t_form"]), 3), "slot": b["slot"], "lane": b["lane"],
+                       "requests": b["n_requests"], "triangles": b["n_triangles"],
+                       "t_form_s": round(b["t_form"], 4),
+                       **{k: round(b[k], 3) for k in ("in_ms", "run_ms", "idle_ms", "out_ms")},
+                       "host_enqueue_ms": round(1e3 * (b["t_enqueued"] - b["t_form"]), 3)} for b in slow]
+    return out
+
+
 def run_served(args):
     small, large = serve_pool()               # process pool, before any CUDA call
     import numpy as np
@@ -769,7 +799,9 @@ def run_served(args):
         span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
         wait = np.array([i["t_admit"] - i["t_submit"] for i in infos])
         serve = np.array([i["t_done"] - i["t_admit"] for i in infos])
+        t_first = min(i["t_submit"] for i in infos)
         return {"requests": len(t), "triangles": int(tri[pick].sum()), "span_s": span,
+                "batch_trace": batch_trace([b for b in srv.batch_log() if b["t_form"] >= t_first]),
                 "queue_ms": {"p50": 1e3 * float(np.percentile(wait, 50)), "p99": 1e3 * float(np.percentile(wait, 99))},
                 "service_ms": {"p50": 1e3 * float(np.percentile(serve, 50)), "p99": 1e3 * float(np.percentile(serve, 99))},
                 "tri_per_s": float(tri[pick].sum()) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
@@ -779,7 +811,7 @@ def run_served(args):
                                      for k, i in enumerate(pick)))}
 
     with polylla.Server(memory_budget=r["budget"], n_slots=args.serve_slots,
-                        max_batch_triangles=args.serve_batch_triangles) as srv:
+                        max_batch_triangles=args.serve_batch_triangles, lane_triangles=args.serve_lane) as srv:
         replay(srv, 1.0, seed=1000 + rank)                     # warm-up, untimed
         dist_barrier(ws)
         st0 = srv.stats()
@@ -787,6 +819,7 @@ def run_served(args):
             main = replay(srv, args.serve_seconds, seed=r["seed"] + rank)
         st = srv.stats()
     batches = int(st["batches"] - st0["batches"])
+    launches = int(st["launches"] - st0["launches"])
     with polylla.Server(memory_budget=r["budget"], n_slots=1, max_batch_meshes=1) as one:
         replay(one, 0.5, seed=2000 + rank)
         base = replay(one, args.serve_baseline_seconds, seed=r["seed"] + rank)
@@ -809,6 +842,7 @@ def run_served(args):
                        "pool": f"{len(small)} small + {len(large)} large seeded meshes in pinned host memory",
                        "memory_budget_bytes": r["budget"], "slots": st["n_slots"],
                        "max_batch_triangles": args.serve_batch_triangles,
+                       "lane_triangles": st["lane_triangles"],
                        "slot_triangles": st["slot_triangles"], "device_bytes": st["device_bytes"],
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
@@ -819,7 +853,7 @@ def run_served(args):
                     "d2h_bytes_per_step": main["d2h_bytes"] // max(1, main["requests"]),
                     "api": "polylla_server_replay: host meshes in, host results out, per request"},
             "roofline": None, "cpu_baseline": None,
-            "gpu_launches": batches * 16, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
+            "gpu_launches": launches, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -352,6 +352,19 @@ int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t 
  * polylla_generate_host).  The host arrays of a request must stay valid
  * and unchanged until it completes.
  *
+ * Copies: the copy engines run one direction's copies in issue order across
+ * all streams, so a small batch's copies would wait behind a large one's.
+ * With n_slots >= 2 and lane_triangles >= 0, slot 0 is a low-latency lane:
+ * it batches only requests of at most lane_triangles triangles whose nine
+ * device-touched arrays (coords, origin, twin and the six results) are
+ * pinned host memory, runs on the device's highest-priority stream, and
+ * moves their data with kernels through host-mapped memory, never through
+ * a copy engine.  The other slots take the remaining requests in arrival
+ * order (and lane requests that have waited more than 5 ms); their data
+ * goes through the copy engines (full duplex), while offsets, metadata and
+ * control blocks of every batch move by kernel.  Pageable requests are
+ * served too, through the copy engines.
+ *
  * Requests are not layout-checked (that would cost a pass per batch), but
  * every origin and twin is range-checked while a batch is packed: an index
  * outside its mesh is replaced by one inside it, so no kernel reads outside
@@ -368,6 +381,8 @@ typedef struct {
     int32_t max_batch_triangles; /* a batch stops growing past this many
                                     triangles (0: the slot's capacity); a single
                                     larger request still runs, alone          */
+    int32_t lane_triangles;    /* largest request of the low-latency lane
+                                  (0: 65,536; negative: no lane)              */
 } polylla_server_options;
 typedef struct {
     int32_t n_vertices, n_triangles, n_halfedges;
@@ -392,6 +407,9 @@ typedef struct {
     double max_batch_ms;         /* the slowest batch (in + run + out on its stream) */
     int64_t max_batch_triangles; /*   its triangles                                */
     int32_t max_batch_requests;  /*   and requests                                 */
+    int64_t launches;            /* kernels launched (18 per batch, 19 per lane batch) */
+    int64_t lane_batches;        /* batches the lane ran                            */
+    int32_t lane_triangles;      /* the lane's request limit (0: no lane)           */
 } polylla_server_stats;
 
 /* Create a server on the current device (allocates all slots; starts the
@@ -411,6 +429,33 @@ int polylla_server_wait(polylla_server *srv, int64_t ticket, polylla_request_inf
 int polylla_server_replay(polylla_server *srv, int32_t n, const polylla_request *reqs,
                           const double *arrival_s, double *latency_s, polylla_request_info *infos);
 int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out);
+
+/* One completed batch, for tracing where a request's time goes.  Host times
+ * are seconds on the server's clock (the one polylla_request_info uses);
+ * stream times are CUDA-event milliseconds on the slot's stream. */
+typedef struct polylla_batch_record {
+    double t_form;         /* scheduler starts forming the batch             */
+    double t_enqueued;     /* copies in, kernels and metadata copy enqueued  */
+    double t_meta_seen;    /* scheduler saw the metadata land                */
+    double t_out_enqueued; /* result copies enqueued                         */
+    double t_done;         /* scheduler saw the results land                 */
+    float in_ms;           /* stream: copies in                              */
+    float run_ms;          /* stream: kernels and metadata copy              */
+    float idle_ms;         /* stream: metadata landed -> result copies start */
+    float out_ms;          /* stream: result copies                          */
+    int64_t n_triangles;
+    int32_t n_requests;
+    int32_t slot;
+    int32_t lane;          /* 1: ran in the low-latency lane (kernel copies) */
+} polylla_batch_record;
+
+/* Copy the most recent min(capacity, kept) completed batches, oldest first,
+ * to records (host array of capacity entries; may be NULL when capacity is
+ * 0); *n_out receives how many were written and *n_total (may be NULL) how
+ * many batches completed since create.  The server keeps the last 65,536.
+ * Errors: INVALID_ARGUMENT (NULL srv or n_out, negative capacity). */
+int polylla_server_get_batch_log(polylla_server *srv, polylla_batch_record *records, int32_t capacity,
+                                 int32_t *n_out, int64_t *n_total);
 /* Finish every queued request, stop the scheduler, free everything. */
 void polylla_server_destroy(polylla_server *srv);
 

@@ -866,7 +866,7 @@ int serve_reserve(polylla_ctx **out, int32_t n_cap, int32_t V_cap, int32_t T_cap
 
 size_t serve_bytes(const polylla_ctx *c) { return c ? c->bytes : 0; }
 
-int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const int32_t *h_off4, cudaStream_t s) {
+int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const int32_t *off4, cudaStream_t s) {
     if (!c || !c->serve || n < 1) return POLYLLA_ERR_INVALID_ARGUMENT;
     c->mesh.V = V;
     c->mesh.T = T;
@@ -877,11 +877,8 @@ int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const 
     c->w.loc_n = n;
     c->w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
     c->w.n_chunk_max = (int32_t)((3 * (int64_t)T + CHUNK - 1) / CHUNK);
-    int32_t *dst[4] = {const_cast<int32_t *>(c->bv.v_off), const_cast<int32_t *>(c->bv.t_off),
-                       const_cast<int32_t *>(c->bv.h_off), const_cast<int32_t *>(c->bv.b_off)};
-    for (int k = 0; k < 4; k++)
-        CK(cudaMemcpyAsync(dst[k], h_off4 + (size_t)k * (n + 1), sizeof(int32_t) * (size_t)(n + 1),
-                           cudaMemcpyHostToDevice, s));
+    launch_serve_offsets(off4, n, const_cast<int32_t *>(c->bv.v_off), const_cast<int32_t *>(c->bv.t_off),
+                         const_cast<int32_t *>(c->bv.h_off), const_cast<int32_t *>(c->bv.b_off), s);
     c->last_stream = s;
     c->timed_last = false;
     return enqueue(c, s, false);

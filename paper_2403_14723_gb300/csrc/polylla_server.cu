@@ -14,6 +14,17 @@
 // slot has its own stream, so one slot's copies overlap another's kernels.
 // Slots and arenas are allocated once, at create, within the memory budget:
 // admission against device memory is admission into a slot.
+//
+// The copy engines run one direction's copies in issue order across all
+// streams, so a small batch's copies wait behind a large batch's.  With two
+// or more slots, slot 0 is therefore a low-latency lane: it takes only
+// requests of at most lane_triangles triangles whose buffers are pinned,
+// runs on the device's highest-priority stream, and moves their data with
+// SM kernels through host-mapped memory (kernels_serve.cu), so no copy
+// engine queue is ever in its path.  The other slots take every other
+// request in arrival order, and a lane request that has waited longer than
+// kStealSeconds.  Offsets, metadata and control blocks of every batch move
+// by kernel too.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -35,6 +46,11 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kMaxSlots = 16;
+constexpr size_t kLogKeep = 65536;  // completed batches kept for polylla_server_get_batch_log
+constexpr int32_t kLaneDefault = 65536;  // lane_triangles when the option is 0
+constexpr double kStealSeconds = 0.005;  // a lane request older than this may join any batch
+constexpr int32_t kLaunchesCE = 18;      // per batch: offsets, 16 of the run, metadata out
+constexpr int32_t kLaunchesLane = 19;    // per lane batch: gather, offsets, 16 of the run, scatter
 
 struct Req {
     polylla_request r{};
@@ -43,6 +59,8 @@ struct Req {
     int status = POLYLLA_OK;
     int32_t P = 0, NF = 0, batch_meshes = 0;
     bool done = false;
+    int8_t mapped = -1;  // -1 not checked yet; 1: every buffer pinned (tab holds their device addresses)
+    ServeTab tab{};
 };
 
 struct Slot {
@@ -50,13 +68,19 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_meta = nullptr, ev_out = nullptr;
     // timing of the batch in flight: start, inputs in, metadata out, results out
-    cudaEvent_t ev_t0 = nullptr, ev_in = nullptr, ev_tm = nullptr, ev_to = nullptr;
-    double host_meta_seen = 0;  // when the scheduler saw the metadata land
+    cudaEvent_t ev_t0 = nullptr, ev_in = nullptr, ev_tm = nullptr, ev_o0 = nullptr, ev_to = nullptr;
+    polylla_batch_record rec{};  // host times of the batch in flight
     double *coords = nullptr;  // device arena: concatenated local arrays
     int32_t *origin = nullptr, *twin = nullptr, *next = nullptr, *prev = nullptr;
     int32_t *h_off = nullptr;  // pinned [4 (n_cap + 1)]: v, t, h, b prefix sums
     int32_t *h_meta = nullptr; // pinned [4 n_cap]
     DevCtrl *h_ctrl = nullptr; // pinned
+    ServeTab *h_tab = nullptr; // pinned [n_cap]: the lane batch's request buffers
+    // device addresses of the pinned arrays above
+    int32_t *d_off = nullptr, *d_meta = nullptr;
+    DevCtrl *d_ctrl = nullptr;
+    ServeTab *d_tab = nullptr;
+    bool lane = false;         // the low-latency lane (slot 0 when enabled)
     int32_t n_cap = 0, V_cap = 0, T_cap = 0, H_cap = 0;
     std::vector<Req *> reqs;
     int state = 0;             // 0 free, 1 batch running, 2 copying results out
@@ -82,6 +106,7 @@ struct polylla_server {
     int32_t max_batch = 4096;
     int32_t max_rotation = 0;
     int64_t max_batch_tri = 0;  // 0: slot capacity
+    int32_t lane_tri = 0;       // 0: no lane
     int n_slots = 0;
     Slot slots[kMaxSlots];
     int64_t device_bytes = 0;
@@ -101,6 +126,9 @@ struct polylla_server {
     double slowest_ms = 0;                  // the slowest batch on its stream, and its size
     int64_t slowest_tri = 0;
     int32_t slowest_n = 0;
+    std::vector<polylla_batch_record> log;  // ring of the last kLogKeep batches
+    int64_t log_total = 0;
+    int64_t launches = 0, lane_batches = 0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void loop();
@@ -108,7 +136,40 @@ struct polylla_server {
     void copy_out(Slot &s);
     void finish(Slot &s, int status);
     void complete(Req *q, int status);
+    bool lane_ok(Req *q);
 };
+
+// Whether every buffer the device touches for q is pinned host memory, and
+// their device addresses (checked once per request).
+bool polylla_server::lane_ok(Req *q) {
+    if (q->mapped < 0) {
+        const void *p[9] = {q->r.mesh.coords,   q->r.mesh.origin,  q->r.mesh.twin,
+                            q->r.result.seeds,  q->r.result.offsets, q->r.result.he_list,
+                            q->r.result.v_list, q->r.result.next,  q->r.result.prev};
+        void *d[9] = {};
+        bool ok = true;
+        for (int k = 0; k < 9 && ok; k++) {
+            cudaPointerAttributes a{};
+            ok = cudaPointerGetAttributes(&a, p[k]) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+                 a.devicePointer != nullptr;
+            d[k] = ok ? a.devicePointer : nullptr;
+        }
+        cudaGetLastError();  // an unregistered pointer leaves no error behind
+        if (ok) {
+            q->tab.coords = static_cast<const double *>(d[0]);
+            q->tab.origin = static_cast<const int32_t *>(d[1]);
+            q->tab.twin = static_cast<const int32_t *>(d[2]);
+            q->tab.seeds = static_cast<int32_t *>(d[3]);
+            q->tab.offsets = static_cast<int32_t *>(d[4]);
+            q->tab.he_list = static_cast<int32_t *>(d[5]);
+            q->tab.v_list = static_cast<int32_t *>(d[6]);
+            q->tab.next = static_cast<int32_t *>(d[7]);
+            q->tab.prev = static_cast<int32_t *>(d[8]);
+        }
+        q->mapped = ok ? 1 : 0;
+    }
+    return q->mapped == 1 && q->r.n_triangles <= lane_tri;
+}
 
 void polylla_server::complete(Req *q, int status) {
     std::lock_guard<std::mutex> g(mu);
@@ -132,12 +193,14 @@ bool polylla_server::launch(Slot &s) {
     {
         std::lock_guard<std::mutex> g(mu);
         int64_t V = 0, T = 0, H = 0;
-        while (!pending.empty() && (int32_t)take.size() < std::min(s.n_cap, max_batch)) {
-            Req *q = pending.front();
+        const double t_now = now();
+        const int32_t cap_n = std::min(s.n_cap, max_batch);
+        for (auto it = pending.begin(); it != pending.end() && (int32_t)take.size() < cap_n;) {
+            Req *q = *it;
             const polylla_request &r = q->r;
             if (r.n_vertices > s.V_cap || r.n_triangles > s.T_cap || r.n_halfedges > s.H_cap) {
                 // larger than any slot: fails now (slots are identical)
-                pending.pop_front();
+                it = pending.erase(it);
                 q->status = POLYLLA_ERR_TOO_LARGE;
                 q->t_admit = q->t_done = now();
                 q->done = true;
@@ -145,13 +208,20 @@ bool polylla_server::launch(Slot &s) {
                 cv_done.notify_all();
                 continue;
             }
+            if (lane_tri > 0) {
+                const bool small = lane_ok(q);
+                if (s.lane != small && (s.lane || t_now - q->t_submit < kStealSeconds)) {
+                    ++it;  // the lane takes lane requests only; the others leave them to it for a while
+                    continue;
+                }
+            }
             if (V + r.n_vertices > s.V_cap || T + r.n_triangles > s.T_cap || H + r.n_halfedges > s.H_cap) break;
             if (!take.empty() && max_batch_tri > 0 && T + r.n_triangles > max_batch_tri) break;
             V += r.n_vertices;
             T += r.n_triangles;
             H += r.n_halfedges;
             take.push_back(q);
-            pending.pop_front();
+            it = pending.erase(it);
         }
     }
     if (take.empty()) return false;
@@ -166,31 +236,68 @@ bool polylla_server::launch(Slot &s) {
         bo[i + 1] = ho[i + 1] - 3 * to[i + 1];
     }
     const double t = now();
+    s.rec = polylla_batch_record{};
+    s.rec.t_form = t;
+    s.rec.n_requests = n;
+    s.rec.n_triangles = to[n];
     s.reqs = take;
     for (Req *q : take) {
         q->t_admit = t;
         q->batch_meshes = n;
     }
+    // lane batches: blocks per request of the copy kernels, from the largest request
+    int32_t bx = 1;
     cudaError_t e = cudaEventRecord(s.ev_t0, s.stream);
-    for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
-        const polylla_request &r = take[i]->r;
-        const size_t Hb = 4 * (size_t)r.n_halfedges;
-        e = cudaMemcpyAsync(s.coords + 2 * (size_t)vo[i], r.mesh.coords, 16 * (size_t)r.n_vertices,
-                            cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.origin + ho[i], r.mesh.origin, Hb, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.twin + ho[i], r.mesh.twin, Hb, cudaMemcpyHostToDevice, s.stream);
-        // next/prev are not read by the method (their interior entries are
-        // rewritten, border entries go back from the host input)
+    if (s.lane) {
+        int32_t h_max = 0;
+        for (int32_t i = 0; i < n; i++) {
+            const Req *q = take[i];
+            s.h_tab[i] = q->tab;
+            h_max = std::max(h_max, q->r.n_halfedges);
+            // border next/prev are the input's (the method leaves them as they are)
+            const size_t n_int = 3 * (size_t)q->r.n_triangles, n_b = (size_t)q->r.n_halfedges - n_int;
+            memcpy(q->r.result.next + n_int, q->r.mesh.next + n_int, 4 * n_b);
+            memcpy(q->r.result.prev + n_int, q->r.mesh.prev + n_int, 4 * n_b);
+        }
+        bx = std::max(1, std::min(64, h_max / 8192));
+        if (e == cudaSuccess) {
+            launch_serve_gather(s.d_tab, s.d_off, n, bx, s.coords, s.origin, s.twin, s.stream);
+            e = cudaGetLastError();
+        }
+    } else {
+        for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
+            const polylla_request &r = take[i]->r;
+            const size_t Hb = 4 * (size_t)r.n_halfedges;
+            e = cudaMemcpyAsync(s.coords + 2 * (size_t)vo[i], r.mesh.coords, 16 * (size_t)r.n_vertices,
+                                cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s.origin + ho[i], r.mesh.origin, Hb, cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s.twin + ho[i], r.mesh.twin, Hb, cudaMemcpyHostToDevice, s.stream);
+            // next/prev are not read by the method (their interior entries are
+            // rewritten, border entries go back from the host input)
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecord(s.ev_in, s.stream);
-    int rc = e == cudaSuccess ? serve_run(s.ctx, n, vo[n], to[n], ho[n], s.h_off, s.stream) : POLYLLA_ERR_CUDA;
+    int rc = e == cudaSuccess ? serve_run(s.ctx, n, vo[n], to[n], ho[n], s.d_off, s.stream) : POLYLLA_ERR_CUDA;
     if (rc == POLYLLA_OK) {
         ServeOutputs o;
         serve_outputs(s.ctx, &o);
-        e = cudaMemcpyAsync(s.h_meta, o.meta, 16 * (size_t)n, cudaMemcpyDeviceToHost, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_ctrl, o.ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s.stream);
-        if (e == cudaSuccess) e = cudaEventRecord(s.ev_meta, s.stream);
-        if (e == cudaSuccess) e = cudaEventRecord(s.ev_tm, s.stream);
+        if (s.lane) {
+            // results straight into the requests' host buffers
+            e = cudaEventRecord(s.ev_tm, s.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(s.ev_o0, s.stream);
+            if (e == cudaSuccess) {
+                launch_serve_scatter(s.d_tab, s.d_off, n, bx, o, s.next, s.prev, to[n], s.d_meta, s.d_ctrl,
+                                     s.stream);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(s.ev_to, s.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(s.ev_out, s.stream);
+        } else {
+            launch_serve_meta_out(o, n, s.d_meta, s.d_ctrl, s.stream);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(s.ev_meta, s.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(s.ev_tm, s.stream);
+        }
         if (e != cudaSuccess) rc = POLYLLA_ERR_CUDA;
     }
     if (rc != POLYLLA_OK) {
@@ -198,10 +305,15 @@ bool polylla_server::launch(Slot &s) {
         finish(s, rc);
         return true;
     }
-    s.state = 1;
+    s.state = s.lane ? 2 : 1;
+    s.rec.t_enqueued = now();
+    if (s.lane) s.rec.t_meta_seen = s.rec.t_out_enqueued = s.rec.t_enqueued;
+    s.rec.lane = s.lane ? 1 : 0;
     {
         std::lock_guard<std::mutex> g(mu);
         batches++;
+        launches += s.lane ? kLaunchesLane : kLaunchesCE;
+        lane_batches += s.lane ? 1 : 0;
     }
     return true;
 }
@@ -217,7 +329,7 @@ void polylla_server::copy_out(Slot &s) {
     serve_outputs(s.ctx, &o);
     const int32_t n = (int32_t)s.reqs.size();
     const int32_t *ho = s.h_off + 2 * (n + 1);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(s.ev_o0, s.stream);
     for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
         Req *q = s.reqs[i];
         polylla_host_result &out = q->r.result;
@@ -243,6 +355,7 @@ void polylla_server::copy_out(Slot &s) {
     }
     if (e == cudaSuccess) e = cudaEventRecord(s.ev_out, s.stream);
     if (e == cudaSuccess) e = cudaEventRecord(s.ev_to, s.stream);
+    s.rec.t_out_enqueued = now();
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s.stream);
         finish(s, POLYLLA_ERR_CUDA);
@@ -262,6 +375,7 @@ void polylla_server::loop() {
             if (s.state == 1) {
                 const cudaError_t q = cudaEventQuery(s.ev_meta);
                 if (q == cudaSuccess) {
+                    s.rec.t_meta_seen = now();
                     copy_out(s);
                     progressed = true;
                 } else if (q != cudaErrorNotReady) {
@@ -273,13 +387,23 @@ void polylla_server::loop() {
                 const cudaError_t q = cudaEventQuery(s.ev_out);
                 if (q == cudaSuccess || q != cudaErrorNotReady) {
                     if (q == cudaSuccess) {
-                        float a = 0, b = 0, c = 0;
+                        float a = 0, b = 0, c = 0, d = 0, i = 0;
                         if (cudaEventElapsedTime(&a, s.ev_t0, s.ev_in) == cudaSuccess &&
                             cudaEventElapsedTime(&b, s.ev_in, s.ev_tm) == cudaSuccess &&
-                            cudaEventElapsedTime(&c, s.ev_tm, s.ev_to) == cudaSuccess) {
-                            int64_t tri = 0;
-                            for (Req *r : s.reqs) tri += r->r.n_triangles;
+                            cudaEventElapsedTime(&c, s.ev_tm, s.ev_to) == cudaSuccess &&
+                            cudaEventElapsedTime(&i, s.ev_tm, s.ev_o0) == cudaSuccess &&
+                            cudaEventElapsedTime(&d, s.ev_o0, s.ev_to) == cudaSuccess) {
+                            const int64_t tri = s.rec.n_triangles;
+                            s.rec.t_done = now();
+                            s.rec.in_ms = a;
+                            s.rec.run_ms = b;
+                            s.rec.idle_ms = i;
+                            s.rec.out_ms = d;
+                            s.rec.slot = k;
                             std::lock_guard<std::mutex> g(mu);
+                            if (log.size() < kLogKeep) log.push_back(s.rec);
+                            else log[(size_t)(log_total % (int64_t)kLogKeep)] = s.rec;
+                            log_total++;
                             t_in += a;
                             t_run += b;
                             t_out += c;
@@ -291,11 +415,26 @@ void polylla_server::loop() {
                             }
                         }
                     }
-                    for (Req *r : s.reqs) {
-                        r->r.result.n_polygons = r->P;
-                        r->r.result.n_frontier = r->NF;
+                    if (s.lane && q == cudaSuccess) {
+                        // the scatter wrote the metadata and control block to pinned memory
+                        const int st = serve_status(*s.h_ctrl);
+                        for (size_t i = 0; i < s.reqs.size(); i++) {
+                            Req *r = s.reqs[i];
+                            r->P = s.h_meta[4 * i];
+                            r->NF = s.h_meta[4 * i + 1];
+                            r->r.result.n_polygons = r->P;
+                            r->r.result.n_frontier = r->NF;
+                            complete(r, st != POLYLLA_OK ? st : r->P < 0 ? POLYLLA_ERR_CAPACITY : POLYLLA_OK);
+                        }
+                        s.reqs.clear();
+                        s.state = 0;
+                    } else {
+                        for (Req *r : s.reqs) {
+                            r->r.result.n_polygons = r->P;
+                            r->r.result.n_frontier = r->NF;
+                        }
+                        finish(s, q == cudaSuccess ? POLYLLA_OK : POLYLLA_ERR_CUDA);
                     }
-                    finish(s, q == cudaSuccess ? POLYLLA_OK : POLYLLA_ERR_CUDA);
                     progressed = true;
                 }
             }
@@ -338,25 +477,31 @@ static void free_slot(Slot &s) {
     if (s.h_off) cudaFreeHost(s.h_off);
     if (s.h_meta) cudaFreeHost(s.h_meta);
     if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
+    if (s.h_tab) cudaFreeHost(s.h_tab);
     if (s.ev_meta) cudaEventDestroy(s.ev_meta);
-    for (cudaEvent_t ev : {s.ev_t0, s.ev_in, s.ev_tm, s.ev_to})
+    for (cudaEvent_t ev : {s.ev_t0, s.ev_in, s.ev_tm, s.ev_o0, s.ev_to})
         if (ev) cudaEventDestroy(ev);
     if (s.ev_out) cudaEventDestroy(s.ev_out);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
 }
 
-static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t T, int32_t H) {
+static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t T, int32_t H, bool lane) {
     s.n_cap = n;
     s.V_cap = V;
     s.T_cap = T;
     s.H_cap = H;
-    cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    s.lane = lane;
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    // the lane's kernels go first whenever SMs free up
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, lane ? greatest : least);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_meta, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_in);
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_tm);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev_o0);
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_to);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.coords, 16 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.origin, 4 * (size_t)H);
@@ -366,6 +511,11 @@ static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_off, sizeof(int32_t) * 4 * ((size_t)n + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_meta, sizeof(int32_t) * 4 * (size_t)n);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_ctrl, sizeof(DevCtrl));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s.h_tab, sizeof(ServeTab) * (size_t)n);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s.d_off, s.h_off, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s.d_meta, s.h_meta, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s.d_ctrl, s.h_ctrl, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&s.d_tab, s.h_tab, 0);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? POLYLLA_ERR_OUT_OF_MEMORY : POLYLLA_ERR_CUDA;
     const int rc = serve_reserve(&s.ctx, n, V, T, H, s.coords, s.origin, s.twin, s.next, s.prev, srv->max_rotation);
     if (rc) return rc;
@@ -391,6 +541,9 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
     srv->max_batch = opt->max_batch_meshes ? opt->max_batch_meshes : 4096;
     srv->max_rotation = opt->max_rotation;
     srv->max_batch_tri = opt->max_batch_triangles;
+    // a lane needs a second slot for everything else
+    srv->lane_tri = srv->n_slots < 2 || opt->lane_triangles < 0 ? 0
+                    : opt->lane_triangles ? opt->lane_triangles : kLaneDefault;
     // slot capacity: the largest T whose slot, with V <= T + 2n and
     // H <= 4T + 2n (bounds for triangulated disks), fits budget / n_slots
     const int64_t per = opt->memory_budget / srv->n_slots;
@@ -407,7 +560,8 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
     }
     const int32_t T = (int32_t)lo, V = (int32_t)(lo + 2 * n), H = (int32_t)(4 * lo + 2 * n);
     int rc = POLYLLA_OK;
-    for (int k = 0; k < srv->n_slots && !rc; k++) rc = make_slot(srv, srv->slots[k], (int32_t)n, V, T, H);
+    for (int k = 0; k < srv->n_slots && !rc; k++)
+        rc = make_slot(srv, srv->slots[k], (int32_t)n, V, T, H, k == 0 && srv->lane_tri > 0);
     if (rc) {
         for (int k = 0; k < srv->n_slots; k++) free_slot(srv->slots[k]);
         delete srv;
@@ -516,6 +670,23 @@ int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out) {
     out->max_batch_ms = srv->slowest_ms;
     out->max_batch_triangles = srv->slowest_tri;
     out->max_batch_requests = srv->slowest_n;
+    out->launches = srv->launches;
+    out->lane_batches = srv->lane_batches;
+    out->lane_triangles = srv->lane_tri;
+    return POLYLLA_OK;
+}
+
+int polylla_server_get_batch_log(polylla_server *srv, polylla_batch_record *records, int32_t capacity,
+                                 int32_t *n_out, int64_t *n_total) {
+    if (!srv || !n_out || capacity < 0 || (capacity > 0 && !records)) return POLYLLA_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> g(srv->mu);
+    const int64_t kept = (int64_t)srv->log.size();
+    const int64_t m = std::min<int64_t>(kept, capacity);
+    // oldest kept record: index 0 until the ring wraps, then the next slot to overwrite
+    const int64_t first = kept < (int64_t)kLogKeep ? 0 : srv->log_total % (int64_t)kLogKeep;
+    for (int64_t i = 0; i < m; i++) records[i] = srv->log[(size_t)((first + kept - m + i) % kept)];
+    *n_out = (int32_t)m;
+    if (n_total) *n_total = srv->log_total;
     return POLYLLA_OK;
 }
 

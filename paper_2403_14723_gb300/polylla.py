@@ -87,7 +87,7 @@ class polylla_tuning(ctypes.Structure):
 class polylla_server_options(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_int64), ("n_slots", ctypes.c_int32),
                 ("max_batch_meshes", ctypes.c_int32), ("max_rotation", ctypes.c_int32),
-                ("max_batch_triangles", ctypes.c_int32)]
+                ("max_batch_triangles", ctypes.c_int32), ("lane_triangles", ctypes.c_int32)]
 
 
 class polylla_request(ctypes.Structure):
@@ -106,7 +106,16 @@ class polylla_server_stats(ctypes.Structure):
                 ("batches", ctypes.c_int64), ("requests_done", ctypes.c_int64), ("busy_seconds", ctypes.c_double),
                 ("mean_in_ms", ctypes.c_double), ("mean_run_ms", ctypes.c_double), ("mean_out_ms", ctypes.c_double),
                 ("max_batch_ms", ctypes.c_double), ("max_batch_triangles", ctypes.c_int64),
-                ("max_batch_requests", ctypes.c_int32)]
+                ("max_batch_requests", ctypes.c_int32), ("launches", ctypes.c_int64),
+                ("lane_batches", ctypes.c_int64), ("lane_triangles", ctypes.c_int32)]
+
+
+class polylla_batch_record(ctypes.Structure):
+    _fields_ = [("t_form", ctypes.c_double), ("t_enqueued", ctypes.c_double), ("t_meta_seen", ctypes.c_double),
+                ("t_out_enqueued", ctypes.c_double), ("t_done", ctypes.c_double), ("in_ms", ctypes.c_float),
+                ("run_ms", ctypes.c_float), ("idle_ms", ctypes.c_float), ("out_ms", ctypes.c_float),
+                ("n_triangles", ctypes.c_int64), ("n_requests", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("lane", ctypes.c_int32)]
 
 
 # every function the header declares, with its ctypes signature
@@ -153,6 +162,9 @@ _SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(polylla_request_info)]),
     "polylla_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_server_stats)]),
+    "polylla_server_get_batch_log": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_batch_record),
+                                                    ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                    ctypes.POINTER(ctypes.c_int64)]),
     "polylla_server_destroy": (None, [ctypes.c_void_p]),
 }
 
@@ -516,22 +528,23 @@ def polylla_lepp_paths(ctx: int, tri, capacity: int, stream=None):
 
 
 class HostRequest:
-    """A mesh in pinned host memory plus pinned result buffers of the
-    capacities a request needs (T, T+1, 3T, 3T, H, H)."""
+    """A mesh in host memory plus result buffers of the capacities a request
+    needs (T, T+1, 3T, 3T, H, H); pinned unless ``pinned=False``."""
 
-    def __init__(self, mesh):
+    def __init__(self, mesh, pinned: bool = True):
         import torch
 
         self.mesh = mesh
         T, H = int(mesh.n_triangles), int(mesh.n_halfedges)
-        self.inp = {k: torch.from_numpy(getattr(mesh, k)).contiguous().pin_memory()
+        pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t.clone())
+        self.inp = {k: pin(torch.from_numpy(getattr(mesh, k)).contiguous())
                     for k in ("coords", "origin", "twin", "next", "prev")}
-        self.out = {"seeds": torch.empty(T, dtype=torch.int32).pin_memory(),
-                    "offsets": torch.empty(T + 1, dtype=torch.int32).pin_memory(),
-                    "he_list": torch.empty(3 * T, dtype=torch.int32).pin_memory(),
-                    "v_list": torch.empty(3 * T, dtype=torch.int32).pin_memory(),
-                    "next": torch.empty(H, dtype=torch.int32).pin_memory(),
-                    "prev": torch.empty(H, dtype=torch.int32).pin_memory()}
+        self.out = {"seeds": pin(torch.empty(T, dtype=torch.int32)),
+                    "offsets": pin(torch.empty(T + 1, dtype=torch.int32)),
+                    "he_list": pin(torch.empty(3 * T, dtype=torch.int32)),
+                    "v_list": pin(torch.empty(3 * T, dtype=torch.int32)),
+                    "next": pin(torch.empty(H, dtype=torch.int32)),
+                    "prev": pin(torch.empty(H, dtype=torch.int32))}
         self.req = polylla_request(
             int(mesh.n_vertices), T, H,
             polylla_host_mesh(*(ctypes.c_void_p(self.inp[k].data_ptr())
@@ -556,10 +569,10 @@ class Server:
     requests on the current device."""
 
     def __init__(self, memory_budget: int, n_slots: int = 3, max_batch_meshes: int = 0, max_rotation: int = 0,
-                 max_batch_triangles: int = 0):
+                 max_batch_triangles: int = 0, lane_triangles: int = 0):
         lib = load_library()
         opt = polylla_server_options(int(memory_budget), int(n_slots), int(max_batch_meshes), int(max_rotation),
-                                     int(max_batch_triangles))
+                                     int(max_batch_triangles), int(lane_triangles))
         h = ctypes.c_void_p()
         _check(lib.polylla_server_create(ctypes.byref(h), ctypes.byref(opt)), "polylla_server_create")
         self.h = h.value
@@ -594,6 +607,15 @@ class Server:
         _check(load_library().polylla_server_get_stats(ctypes.c_void_p(self.h), ctypes.byref(st)),
                "polylla_server_get_stats")
         return {k: getattr(st, k) for k, _ in polylla_server_stats._fields_}
+
+    def batch_log(self, capacity: int = 65536) -> list:
+        """The most recent completed batches, oldest first (one dict each)."""
+        recs = (polylla_batch_record * capacity)()
+        n = ctypes.c_int32()
+        tot = ctypes.c_int64()
+        _check(load_library().polylla_server_get_batch_log(ctypes.c_void_p(self.h), recs, capacity, ctypes.byref(n),
+                                                           ctypes.byref(tot)), "polylla_server_get_batch_log")
+        return [{k: getattr(recs[i], k) for k, _ in polylla_batch_record._fields_} for i in range(n.value)]
 
     def close(self):
         if self.h:

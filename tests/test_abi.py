@@ -90,6 +90,7 @@ def test_null_arguments_rejected_without_gpu(lib_path):
     assert lib.polylla_server_create(ctypes.byref(srv), ctypes.byref(bad)) == -1
     assert lib.polylla_server_submit(None, None, None) == -1
     assert lib.polylla_server_get_stats(None, None) == -1
+    assert lib.polylla_server_get_batch_log(None, None, 0, None, None) == -1
     assert lib.polylla_server_replay(None, 0, None, None, None, None) == -1
 
 

@@ -59,6 +59,46 @@ def test_served_requests_match_oracle_alone_and_in_the_mix():
         st = srv.stats()
         assert st["requests_done"] == len(meshes) + 3 and st["batches"] >= 4
         assert st["device_bytes"] <= 3 << 30
+        log = srv.batch_log()
+        assert len(log) == st["batches"]
+        assert sum(b["n_requests"] for b in log) == len(meshes) + 3
+        assert sum(b["n_triangles"] for b in log) == sum(m.n_triangles for m in meshes) + \
+            sum(meshes[i].n_triangles for i in (0, 4, len(meshes) - 1))
+        for b in log:
+            assert b["t_form"] <= b["t_enqueued"] <= b["t_meta_seen"] <= b["t_out_enqueued"] <= b["t_done"]
+            assert min(b["in_ms"], b["run_ms"], b["idle_ms"], b["out_ms"]) >= 0 and 0 <= b["slot"] < st["n_slots"]
+        assert srv.batch_log(2) == log[-2:]
+        # small pinned requests ran in the lane (kernel copies), the large one outside it
+        assert st["lane_triangles"] == 65536 and st["lane_batches"] >= 1
+        assert any(b["lane"] == 1 for b in log) and any(b["lane"] == 0 for b in log)
+        assert st["launches"] == 19 * st["lane_batches"] + 18 * (st["batches"] - st["lane_batches"])
+
+
+def test_copy_paths_give_identical_results():
+    """The same requests through the lane (kernel copies through host-mapped
+    memory), through the copy engines (pageable buffers, or no lane), alone
+    and mixed: every result is the oracle's, bit for bit."""
+    build.build_library()
+    meshes = [meshgen.exact_grid(7), meshgen.perturbed_grid(60, 0.3, seed=31)]
+    meshes += meshgen.random_batch(10, t_min=500, t_max=60_000, seed=52)
+    want = [oracle.run_mesh(m) for m in meshes]
+    for lane, pinned in ((0, True), (0, False), (-1, True), (4000, True)):
+        with polylla.Server(memory_budget=1 << 30, n_slots=3, lane_triangles=lane) as srv:
+            reqs = [polylla.HostRequest(m, pinned=pinned) for m in meshes]
+            infos = [srv.wait(t) for t in [srv.submit(r) for r in reqs]]
+            st = srv.stats()
+            log = srv.batch_log()
+        tag = f"lane={lane} pinned={pinned}"
+        for m, hr, info, r in zip(meshes, reqs, infos, want):
+            _check(m, info, hr.result(info), r, f"{tag} {m.name}")
+        n_lane = sum(b["n_requests"] for b in log if b["lane"])
+        if lane < 0 or not pinned:
+            assert n_lane == 0 and st["lane_batches"] == 0, tag          # no lane, or nothing it may take
+        else:
+            limit = lane or 65536
+            small = sum(m.n_triangles <= limit for m in meshes)
+            assert 0 < n_lane <= small, tag                               # lane requests only (some may be taken by others)
+            assert all(b["n_triangles"] <= limit * b["n_requests"] for b in log if b["lane"]), tag
 
 
 def test_replay_poisson_trace():
