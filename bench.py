@@ -810,6 +810,22 @@ def run_served(args):
                 "d2h_bytes": int(sum(4 * (2 * infos[k]["n_polygons"] + 1 + 2 * infos[k]["n_frontier"] + 6 * pool[i].n_triangles)
                                      for k, i in enumerate(pick)))}
 
+    # the copy engines' rate on an idle link, from the pool's largest pinned request
+    big = max(range(len(pool)), key=lambda i: pool[i].n_halfedges)
+    src = hrs[big].inp["origin"]
+    dev = torch.empty(src.shape, dtype=src.dtype, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(2):
+        ev[0].record()
+        dev.copy_(src, non_blocking=True)
+        ev[1].record()
+        hrs[big].out["next"][: src.shape[0]].copy_(dev, non_blocking=True)
+        ev[2].record()
+        torch.cuda.synchronize()
+    nbytes = src.numel() * src.element_size()
+    copy_check = {"bytes": nbytes, "h2d_gbs": nbytes / (ev[0].elapsed_time(ev[1]) * 1e6),
+                  "d2h_gbs": nbytes / (ev[1].elapsed_time(ev[2]) * 1e6)}
+    del dev
     with polylla.Server(memory_budget=r["budget"], n_slots=args.serve_slots,
                         max_batch_triangles=args.serve_batch_triangles, lane_triangles=args.serve_lane) as srv:
         replay(srv, 1.0, seed=1000 + rank)                     # warm-up, untimed
@@ -846,7 +862,7 @@ def run_served(args):
                        "slot_triangles": st["slot_triangles"], "device_bytes": st["device_bytes"],
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
-            "served": main, "server_stats": st,
+            "served": main, "server_stats": st, "copy_check": copy_check,
             "one_mesh_at_a_time": dict(base, how="same server loop with one slot and one mesh per batch, "
                                                   f"{args.serve_baseline_seconds:g} s of the same recipe"),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": main["h2d_bytes"] // max(1, main["requests"]),
