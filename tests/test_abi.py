@@ -102,3 +102,36 @@ def test_missing_library_fails_loudly(tmp_path):
     """No CPU fallback: without the built library every call raises."""
     with pytest.raises(RuntimeError, match="not built"):
         polylla.load_library(str(tmp_path / "libpolylla_missing.so"))
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (a C program built from include/polylla.h prints them)."""
+    import shutil
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(polylla, n) for n in dir(polylla)
+               if n.startswith("polylla_") and isinstance(getattr(polylla, n), type)
+               and issubclass(getattr(polylla, n), ctypes.Structure)]
+    assert len(structs) >= 13
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "polylla.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'    printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(build.ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                                text=True).stdout.splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, f"{name}.{f}"
