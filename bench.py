@@ -862,7 +862,7 @@ def run_served(args):
                        "slot_triangles": st["slot_triangles"], "device_bytes": st["device_bytes"],
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
-            "served": main, "server_stats": st, "copy_check": copy_check,
+            "served": main, "server_stats": st, "copy_check": copy_check, "batches": batches,
             "one_mesh_at_a_time": dict(base, how="same server loop with one slot and one mesh per batch, "
                                                   f"{args.serve_baseline_seconds:g} s of the same recipe"),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": main["h2d_bytes"] // max(1, main["requests"]),

@@ -6,12 +6,12 @@
 // order, as many waiting requests as fit the slot's capacity (meshes,
 // triangles, vertices, half-edges), copies their coords, origin and twin
 // into the slot's device arena (the method never reads next/prev), runs the
-// batch (pack, the method's stages, unpack, per-mesh metadata) and copies
-// the per-mesh metadata back.  When that has landed it copies each
-// request's CSR slices and interior next/prev back into the request's host
-// buffers (border entries are the input's, copied on the host); when those
-// land the requests complete.  Each
-// slot has its own stream, so one slot's copies overlap another's kernels.
+// batch (pack, the method's stages, unpack, per-mesh metadata) and moves
+// the per-mesh metadata to pinned host memory.  When that has landed it
+// copies each request's CSR slices and interior next/prev back into the
+// request's host buffers (border entries are the input's, copied on the
+// host); when those land the requests complete.  Each slot has its own
+// stream, so one slot's copies overlap another's kernels.
 // Slots and arenas are allocated once, at create, within the memory budget:
 // admission against device memory is admission into a slot.
 //
