@@ -761,9 +761,19 @@ def batch_trace(log):
         "host_meta_wait_ms": [1e3 * (b["t_meta_seen"] - b["t_enqueued"]) for b in log],
         "host_out_wait_ms": [1e3 * (b["t_done"] - b["t_out_enqueued"]) for b in log],
         "total_ms": [1e3 * (b["t_done"] - b["t_form"]) for b in log],
+        # scheduler time spent enqueueing the result copies of a copy-engine batch
+        "host_out_enqueue_ms": [1e3 * (b["t_out_enqueued"] - b["t_meta_seen"]) for b in log],
+        # the slot's stream began the batch this long after the scheduler enqueued it
+        "stream_start_delay_ms": [1e3 * (b["t_stream_start"] - b["t_form"]) for b in log if b["t_stream_start"] > 0],
+        # the scheduler saw the metadata this long after the stream finished it
+        "meta_notice_delay_ms": [1e3 * (b["t_meta_seen"] - b["t_meta_landed"]) for b in log
+                                 if b["t_meta_landed"] > 0 and not b["lane"]],
+        # host-observed time not covered by the batch's stream segments
+        "host_gap_ms": [1e3 * (b["t_done"] - b["t_form"]) - (b["in_ms"] + b["run_ms"] + b["idle_ms"] + b["out_ms"])
+                        for b in log],
     }
     out = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "max": float(np.max(v))}
-           for k, v in seg.items()}
+           for k, v in seg.items() if v}
     slow = sorted(log, key=lambda b: b["t_done"] - b["t_form"])[-5:]
     out["batches"] = len(log)
     out["lane_batches"] = sum(1 for b in log if b["lane"])
@@ -771,6 +781,11 @@ def batch_trace(log):
                        "requests": b["n_requests"], "triangles": b["n_triangles"],
                        "t_form_s": round(b["t_form"], 4),
                        **{k: round(b[k], 3) for k in ("in_ms", "run_ms", "idle_ms", "out_ms")},
+                       "host_meta_wait_ms": round(1e3 * (b["t_meta_seen"] - b["t_enqueued"]), 3),
+                       "host_out_enqueue_ms": round(1e3 * (b["t_out_enqueued"] - b["t_meta_seen"]), 3),
+                       "host_out_wait_ms": round(1e3 * (b["t_done"] - b["t_out_enqueued"]), 3),
+                       "stream_start_delay_ms": round(1e3 * (b["t_stream_start"] - b["t_form"]), 3),
+                       "meta_notice_delay_ms": round(1e3 * (b["t_meta_seen"] - b["t_meta_landed"]), 3),
                        "host_enqueue_ms": round(1e3 * (b["t_enqueued"] - b["t_form"]), 3)} for b in slow]
     return out
 

@@ -432,7 +432,10 @@ int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out);
 
 /* One completed batch, for tracing where a request's time goes.  Host times
  * are seconds on the server's clock (the one polylla_request_info uses);
- * stream times are CUDA-event milliseconds on the slot's stream. */
+ * stream times are CUDA-event milliseconds on the slot's stream;
+ * t_stream_start and t_meta_landed are stream events placed on the
+ * server's clock through one reference event recorded at create (within a
+ * few microseconds). */
 typedef struct polylla_batch_record {
     double t_form;         /* scheduler starts forming the batch             */
     double t_enqueued;     /* copies in, kernels and metadata copy enqueued  */
@@ -447,6 +450,8 @@ typedef struct polylla_batch_record {
     int32_t n_requests;
     int32_t slot;
     int32_t lane;          /* 1: ran in the low-latency lane (kernel copies) */
+    double t_stream_start; /* the slot's stream began the batch          */
+    double t_meta_landed;  /* the stream finished kernels and metadata   */
 } polylla_batch_record;
 
 /* Copy the most recent min(capacity, kept) completed batches, oldest first,

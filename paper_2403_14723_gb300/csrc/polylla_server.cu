@@ -111,6 +111,8 @@ struct polylla_server {
     Slot slots[kMaxSlots];
     int64_t device_bytes = 0;
     Clock::time_point t0;
+    cudaEvent_t ev_ref = nullptr;  // recorded at create; puts stream events on the server's clock
+    double t_ref = 0;
 
     std::mutex mu;
     std::condition_variable cv_submit, cv_done;
@@ -400,6 +402,12 @@ void polylla_server::loop() {
                             s.rec.idle_ms = i;
                             s.rec.out_ms = d;
                             s.rec.slot = k;
+                            float r0 = 0, r1 = 0;
+                            if (ev_ref && cudaEventElapsedTime(&r0, ev_ref, s.ev_t0) == cudaSuccess &&
+                                cudaEventElapsedTime(&r1, ev_ref, s.ev_tm) == cudaSuccess) {
+                                s.rec.t_stream_start = t_ref + 1e-3 * r0;
+                                s.rec.t_meta_landed = t_ref + 1e-3 * r1;
+                            }
                             std::lock_guard<std::mutex> g(mu);
                             if (log.size() < kLogKeep) log.push_back(s.rec);
                             else log[(size_t)(log_total % (int64_t)kLogKeep)] = s.rec;
@@ -568,6 +576,15 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
         return rc;
     }
     srv->t0 = Clock::now();
+    // reference event: its completion, seen by a synchronize, is t_ref on the server's clock
+    if (cudaEventCreate(&srv->ev_ref) == cudaSuccess && cudaEventRecord(srv->ev_ref, srv->slots[0].stream) == cudaSuccess &&
+        cudaEventSynchronize(srv->ev_ref) == cudaSuccess) {
+        srv->t_ref = srv->now();
+    } else {
+        if (srv->ev_ref) cudaEventDestroy(srv->ev_ref);
+        srv->ev_ref = nullptr;
+        cudaGetLastError();
+    }
     srv->sched = std::thread([srv] { srv->loop(); });
     *out = srv;
     return POLYLLA_OK;
@@ -699,6 +716,7 @@ void polylla_server_destroy(polylla_server *srv) {
     srv->cv_submit.notify_all();
     if (srv->sched.joinable()) srv->sched.join();
     for (int k = 0; k < srv->n_slots; k++) free_slot(srv->slots[k]);
+    if (srv->ev_ref) cudaEventDestroy(srv->ev_ref);
     for (auto &kv : srv->reqs) delete kv.second;
     delete srv;
 }

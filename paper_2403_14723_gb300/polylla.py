@@ -115,7 +115,7 @@ class polylla_batch_record(ctypes.Structure):
                 ("t_out_enqueued", ctypes.c_double), ("t_done", ctypes.c_double), ("in_ms", ctypes.c_float),
                 ("run_ms", ctypes.c_float), ("idle_ms", ctypes.c_float), ("out_ms", ctypes.c_float),
                 ("n_triangles", ctypes.c_int64), ("n_requests", ctypes.c_int32), ("slot", ctypes.c_int32),
-                ("lane", ctypes.c_int32)]
+                ("lane", ctypes.c_int32), ("t_stream_start", ctypes.c_double), ("t_meta_landed", ctypes.c_double)]
 
 
 # every function the header declares, with its ctypes signature
