@@ -461,9 +461,10 @@ def run_gb300(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "polylla_generate_host (pinned host buffers, copies inside the timed region)"}
         # the same steps as a stream of requests through the serving loop:
-        # one step's copies in overlap another's copies out
+        # one step's copies in overlap another's copies out (no small
+        # requests here, so no low-latency lane: all three slots take them)
         hr = polylla.HostRequest(mesh)
-        with polylla.Server(memory_budget=SERVE_RECIPE["budget"], n_slots=3) as srv:
+        with polylla.Server(memory_budget=SERVE_RECIPE["budget"], n_slots=3, lane_triangles=-1) as srv:
             srv.replay([hr] * 2, [0.0, 0.0])
             dist_barrier(ws)
             rc, lat, infos = srv.replay([hr] * e_steps, [0.0] * e_steps)
@@ -851,7 +852,7 @@ def run_served(args):
         st = srv.stats()
     batches = int(st["batches"] - st0["batches"])
     launches = int(st["launches"] - st0["launches"])
-    with polylla.Server(memory_budget=r["budget"], n_slots=1, max_batch_meshes=1) as one:
+    with polylla.Server(memory_budget=r["budget"], n_slots=1, max_batch_meshes=1, lane_triangles=-1) as one:
         replay(one, 0.5, seed=2000 + rank)
         base = replay(one, args.serve_baseline_seconds, seed=r["seed"] + rank)
     value = main["tri_per_s"]
