@@ -460,7 +460,7 @@ def run_gb300(args):
                "api": "polylla_generate_host (pinned host buffers, copies inside the timed region)"}
         # the same steps as a stream of requests through the serving loop:
         # one step's copies in overlap another's copies out (no small
-        # requests here, so no low-latency lane: all three slots take them)
+        # requests here, so no low-latency lane)
         hr = polylla.HostRequest(mesh)
         with polylla.Server(memory_budget=SERVE_RECIPE["budget"], n_slots=3, lane_triangles=-1) as srv:
             srv.replay([hr] * 2, [0.0, 0.0])

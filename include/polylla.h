@@ -341,10 +341,11 @@ int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t 
  * batch a slot forms -- no request waits for a fixed batch to fill.
  *
  * Memory: the server holds at most memory_budget bytes of device memory,
- * split into n_slots slots of equal capacity (triangles, vertices, half-
- * edges, meshes), all allocated at create; a batch is admitted into a slot
- * only while it fits the slot's capacity.  A request larger than one slot
- * completes at once with POLYLLA_ERR_TOO_LARGE.
+ * split into the lane (below) and n_slots copy-engine slots of equal
+ * capacity (triangles, vertices, half-edges, meshes), all allocated at
+ * create; a batch is admitted into a slot only while it fits the slot's
+ * capacity.  A request larger than a copy-engine slot (and not a lane
+ * request) completes with POLYLLA_ERR_TOO_LARGE.
  *
  * A request's result is exactly what polylla_generate_host gives for the
  * mesh alone, whatever it was batched with: CSR and next/prev in the
@@ -354,16 +355,18 @@ int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t 
  *
  * Copies: the copy engines run one direction's copies in issue order across
  * all streams, so a small batch's copies would wait behind a large one's.
- * With n_slots >= 2 and lane_triangles >= 0, slot 0 is a low-latency lane:
- * it batches only requests of at most lane_triangles triangles whose nine
- * device-touched arrays (coords, origin, twin and the six results) are
- * pinned host memory, runs on the device's highest-priority stream, and
- * moves their data with kernels through host-mapped memory, never through
- * a copy engine.  The other slots take the remaining requests in arrival
- * order (and lane requests that have waited more than 5 ms); their data
- * goes through the copy engines (full duplex), while offsets, metadata and
- * control blocks of every batch move by kernel.  Pageable requests are
- * served too, through the copy engines.
+ * Unless lane_triangles < 0 the server adds a low-latency lane (slot 0) to
+ * the n_slots copy-engine slots: a small slot (room for 16 requests of
+ * lane_triangles, within budget / (n_slots + 1)) that batches only
+ * requests of at most lane_triangles triangles whose nine device-touched
+ * arrays (coords, origin, twin and the six results) are pinned host
+ * memory, runs on the device's highest-priority stream, and moves their
+ * data with kernels through host-mapped memory, never through a copy
+ * engine.  The copy-engine slots split the rest of the budget and take the
+ * remaining requests in arrival order (and lane requests that have waited
+ * more than 5 ms); their data goes through the copy engines (full duplex),
+ * while offsets, metadata and control blocks of every batch move by
+ * kernel.  Pageable requests are served too, through the copy engines.
  *
  * Requests are not layout-checked (that would cost a pass per batch), but
  * every origin and twin is range-checked while a batch is packed: an index
@@ -375,7 +378,8 @@ int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t 
 typedef struct polylla_server polylla_server;
 typedef struct {
     int64_t memory_budget;     /* device bytes the server may hold (> 0)        */
-    int32_t n_slots;           /* batches in flight, >= 1 (0: 3)                 */
+    int32_t n_slots;           /* copy-engine batches in flight, 1..16 (0: 3);
+                                  the lane, when on, is one more slot          */
     int32_t max_batch_meshes;  /* meshes per batch, >= 1 (0: 4096)               */
     int32_t max_rotation;      /* as polylla_options (0: 4096)                   */
     int32_t max_batch_triangles; /* a batch stops growing past this many
@@ -396,8 +400,8 @@ typedef struct {
     double t_submit, t_admit, t_done; /* seconds on the server's steady clock      */
 } polylla_request_info;
 typedef struct {
-    int32_t n_slots;
-    int32_t slot_triangles;      /* capacity of one slot                           */
+    int32_t n_slots;             /* slots, the lane included                       */
+    int32_t slot_triangles;      /* capacity of one copy-engine slot               */
     int64_t device_bytes;        /* device memory held                             */
     int64_t batches, requests_done;
     double busy_seconds;         /* time with at least one batch in flight         */
@@ -410,6 +414,7 @@ typedef struct {
     int64_t launches;            /* kernels launched (18 per batch, 19 per lane batch) */
     int64_t lane_batches;        /* batches the lane ran                            */
     int32_t lane_triangles;      /* the lane's request limit (0: no lane)           */
+    int32_t lane_slot_triangles; /* capacity of the lane slot (0: no lane)          */
 } polylla_server_stats;
 
 /* Create a server on the current device (allocates all slots; starts the

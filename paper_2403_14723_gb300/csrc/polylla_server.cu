@@ -16,15 +16,15 @@
 // admission against device memory is admission into a slot.
 //
 // The copy engines run one direction's copies in issue order across all
-// streams, so a small batch's copies wait behind a large batch's.  With two
-// or more slots, slot 0 is therefore a low-latency lane: it takes only
-// requests of at most lane_triangles triangles whose buffers are pinned,
-// runs on the device's highest-priority stream, and moves their data with
-// SM kernels through host-mapped memory (kernels_serve.cu), so no copy
-// engine queue is ever in its path.  The other slots take every other
-// request in arrival order, and a lane request that has waited longer than
-// kStealSeconds.  Offsets, metadata and control blocks of every batch move
-// by kernel too.
+// streams, so a small batch's copies wait behind a large batch's.  Unless
+// disabled, slot 0 is therefore a low-latency lane, one more (small) slot
+// beside the copy-engine slots: it takes only requests of at most
+// lane_triangles triangles whose buffers are pinned, runs on the device's
+// highest-priority stream, and moves their data with SM kernels through
+// host-mapped memory (kernels_serve.cu), so no copy engine queue is ever in
+// its path.  The copy-engine slots take every other request in arrival
+// order, and a lane request that has waited longer than kStealSeconds.
+// Offsets, metadata and control blocks of every batch move by kernel too.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -45,7 +45,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kMaxSlots = 16;
+constexpr int kMaxCeSlots = 16;           // copy-engine slots
+constexpr int kMaxSlots = kMaxCeSlots + 1; // and the lane
+constexpr int64_t kLaneBatch = 16;        // the lane slot holds 16 requests of the lane's largest size
 constexpr size_t kLogKeep = 65536;  // completed batches kept for polylla_server_get_batch_log
 constexpr int32_t kLaneDefault = 65536;  // lane_triangles when the option is 0
 constexpr double kStealSeconds = 0.005;  // a lane request older than this may join any batch
@@ -106,7 +108,7 @@ struct polylla_server {
     int32_t max_batch = 4096;
     int32_t max_rotation = 0;
     int64_t max_batch_tri = 0;  // 0: slot capacity
-    int32_t lane_tri = 0;       // 0: no lane
+    int32_t lane_tri = 0;       // 0: no lane; else the lane is slots[0]
     int n_slots = 0;
     Slot slots[kMaxSlots];
     int64_t device_bytes = 0;
@@ -170,7 +172,9 @@ bool polylla_server::lane_ok(Req *q) {
         }
         q->mapped = ok ? 1 : 0;
     }
-    return q->mapped == 1 && q->r.n_triangles <= lane_tri;
+    const Slot &l = slots[0];
+    return q->mapped == 1 && q->r.n_triangles <= lane_tri && q->r.n_vertices <= l.V_cap &&
+           q->r.n_halfedges <= l.H_cap;
 }
 
 void polylla_server::complete(Req *q, int status) {
@@ -200,8 +204,18 @@ bool polylla_server::launch(Slot &s) {
         for (auto it = pending.begin(); it != pending.end() && (int32_t)take.size() < cap_n;) {
             Req *q = *it;
             const polylla_request &r = q->r;
+            const bool small = lane_tri > 0 && lane_ok(q);
+            if (lane_tri > 0 && s.lane != small && (s.lane || t_now - q->t_submit < kStealSeconds)) {
+                ++it;  // the lane takes lane requests only; the others leave them to it for a while
+                continue;
+            }
             if (r.n_vertices > s.V_cap || r.n_triangles > s.T_cap || r.n_halfedges > s.H_cap) {
-                // larger than any slot: fails now (slots are identical)
+                if (small) {
+                    ++it;  // fits the lane (checked by lane_ok), not this slot
+                    continue;
+                }
+                // larger than any slot (the copy-engine slots are identical and
+                // the largest): fails now
                 it = pending.erase(it);
                 q->status = POLYLLA_ERR_TOO_LARGE;
                 q->t_admit = q->t_done = now();
@@ -209,13 +223,6 @@ bool polylla_server::launch(Slot &s) {
                 done_count++;
                 cv_done.notify_all();
                 continue;
-            }
-            if (lane_tri > 0) {
-                const bool small = lane_ok(q);
-                if (s.lane != small && (s.lane || t_now - q->t_submit < kStealSeconds)) {
-                    ++it;  // the lane takes lane requests only; the others leave them to it for a while
-                    continue;
-                }
             }
             if (V + r.n_vertices > s.V_cap || T + r.n_triangles > s.T_cap || H + r.n_halfedges > s.H_cap) break;
             if (!take.empty() && max_batch_tri > 0 && T + r.n_triangles > max_batch_tri) break;
@@ -536,7 +543,7 @@ extern "C" {
 int polylla_server_create(polylla_server **out, const polylla_server_options *opt) {
     if (!out) return POLYLLA_ERR_INVALID_ARGUMENT;
     *out = nullptr;
-    if (!opt || opt->memory_budget <= 0 || opt->n_slots < 0 || opt->n_slots > kMaxSlots || opt->max_batch_meshes < 0 ||
+    if (!opt || opt->memory_budget <= 0 || opt->n_slots < 0 || opt->n_slots > kMaxCeSlots || opt->max_batch_meshes < 0 ||
         opt->max_rotation < 0 || opt->max_batch_triangles < 0)
         return POLYLLA_ERR_INVALID_ARGUMENT;
     polylla_server *srv = new (std::nothrow) polylla_server();
@@ -545,31 +552,43 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
         delete srv;
         return POLYLLA_ERR_CUDA;
     }
-    srv->n_slots = opt->n_slots ? opt->n_slots : 3;
+    const int n_ce = opt->n_slots ? opt->n_slots : 3;
     srv->max_batch = opt->max_batch_meshes ? opt->max_batch_meshes : 4096;
     srv->max_rotation = opt->max_rotation;
     srv->max_batch_tri = opt->max_batch_triangles;
-    // a lane needs a second slot for everything else
-    srv->lane_tri = srv->n_slots < 2 || opt->lane_triangles < 0 ? 0
-                    : opt->lane_triangles ? opt->lane_triangles : kLaneDefault;
-    // slot capacity: the largest T whose slot, with V <= T + 2n and
-    // H <= 4T + 2n (bounds for triangulated disks), fits budget / n_slots
-    const int64_t per = opt->memory_budget / srv->n_slots;
+    const int64_t lane_req = opt->lane_triangles < 0 ? 0 : opt->lane_triangles ? opt->lane_triangles : kLaneDefault;
     const int64_t n = srv->max_batch;
-    int64_t lo = 0, hi = 500000000;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) / 2;
-        if (slot_bytes(n, mid + 2 * n, mid, 4 * mid + 2 * n) <= per) lo = mid;
-        else hi = mid - 1;
-    }
-    if (lo < 1) {
+    // slot capacity: the largest T (at most t_max) whose slot, with
+    // V <= T + 2n and H <= 4T + 2n (bounds for triangulated disks), fits bytes
+    auto fit = [n](int64_t bytes, int64_t t_max) {
+        int64_t lo = 0, hi = t_max;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (slot_bytes(n, mid + 2 * n, mid, 4 * mid + 2 * n) <= bytes) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    // the lane is one more, small slot: kLaneBatch requests of its largest
+    // size, within a share of the budget; the copy-engine slots split the rest
+    int64_t T_lane = lane_req > 0 ? fit(opt->memory_budget / (n_ce + 1), kLaneBatch * lane_req) : 0;
+    const int64_t lane_bytes = T_lane > 0 ? slot_bytes(n, T_lane + 2 * n, T_lane, 4 * T_lane + 2 * n) : 0;
+    const int64_t T_ce = fit((opt->memory_budget - lane_bytes) / n_ce, 500000000);
+    if (T_ce < 1) {
         delete srv;
         return POLYLLA_ERR_INVALID_ARGUMENT;
     }
-    const int32_t T = (int32_t)lo, V = (int32_t)(lo + 2 * n), H = (int32_t)(4 * lo + 2 * n);
+    srv->lane_tri = T_lane > 0 ? (int32_t)std::min(lane_req, T_lane) : 0;
+    srv->n_slots = n_ce + (srv->lane_tri > 0 ? 1 : 0);
+    const int32_t T = (int32_t)T_ce, V = (int32_t)(T_ce + 2 * n), H = (int32_t)(4 * T_ce + 2 * n);
     int rc = POLYLLA_OK;
-    for (int k = 0; k < srv->n_slots && !rc; k++)
-        rc = make_slot(srv, srv->slots[k], (int32_t)n, V, T, H, k == 0 && srv->lane_tri > 0);
+    for (int k = 0; k < srv->n_slots && !rc; k++) {
+        if (k == 0 && srv->lane_tri > 0)
+            rc = make_slot(srv, srv->slots[k], (int32_t)n, (int32_t)(T_lane + 2 * n), (int32_t)T_lane,
+                           (int32_t)(4 * T_lane + 2 * n), true);
+        else
+            rc = make_slot(srv, srv->slots[k], (int32_t)n, V, T, H, false);
+    }
     if (rc) {
         for (int k = 0; k < srv->n_slots; k++) free_slot(srv->slots[k]);
         delete srv;
@@ -675,7 +694,7 @@ int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out) {
     if (!srv || !out) return POLYLLA_ERR_INVALID_ARGUMENT;
     std::lock_guard<std::mutex> g(srv->mu);
     out->n_slots = srv->n_slots;
-    out->slot_triangles = srv->slots[0].T_cap;
+    out->slot_triangles = srv->slots[srv->n_slots - 1].T_cap;  // a copy-engine slot
     out->device_bytes = srv->device_bytes;
     out->batches = srv->batches;
     out->requests_done = srv->done_count;
@@ -690,6 +709,7 @@ int polylla_server_get_stats(polylla_server *srv, polylla_server_stats *out) {
     out->launches = srv->launches;
     out->lane_batches = srv->lane_batches;
     out->lane_triangles = srv->lane_tri;
+    out->lane_slot_triangles = srv->lane_tri > 0 ? srv->slots[0].T_cap : 0;
     return POLYLLA_OK;
 }
 

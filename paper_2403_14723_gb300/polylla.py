@@ -107,7 +107,8 @@ class polylla_server_stats(ctypes.Structure):
                 ("mean_in_ms", ctypes.c_double), ("mean_run_ms", ctypes.c_double), ("mean_out_ms", ctypes.c_double),
                 ("max_batch_ms", ctypes.c_double), ("max_batch_triangles", ctypes.c_int64),
                 ("max_batch_requests", ctypes.c_int32), ("launches", ctypes.c_int64),
-                ("lane_batches", ctypes.c_int64), ("lane_triangles", ctypes.c_int32)]
+                ("lane_batches", ctypes.c_int64), ("lane_triangles", ctypes.c_int32),
+                ("lane_slot_triangles", ctypes.c_int32)]
 
 
 class polylla_batch_record(ctypes.Structure):

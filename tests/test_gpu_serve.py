@@ -70,6 +70,7 @@ def test_served_requests_match_oracle_alone_and_in_the_mix():
         assert srv.batch_log(2) == log[-2:]
         # small pinned requests ran in the lane (kernel copies), the large one outside it
         assert st["lane_triangles"] == 65536 and st["lane_batches"] >= 1
+        assert st["n_slots"] == 4 and st["lane_slot_triangles"] >= 65536    # three copy-engine slots and the lane
         assert any(b["lane"] == 1 for b in log) and any(b["lane"] == 0 for b in log)
         assert st["launches"] == 19 * st["lane_batches"] + 18 * (st["batches"] - st["lane_batches"])
 
@@ -92,6 +93,7 @@ def test_copy_paths_give_identical_results():
         for m, hr, info, r in zip(meshes, reqs, infos, want):
             _check(m, info, hr.result(info), r, f"{tag} {m.name}")
         n_lane = sum(b["n_requests"] for b in log if b["lane"])
+        assert st["n_slots"] == (3 if lane < 0 else 4), tag
         if lane < 0 or not pinned:
             assert n_lane == 0 and st["lane_batches"] == 0, tag          # no lane, or nothing it may take
         else:
