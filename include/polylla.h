@@ -417,6 +417,21 @@ typedef struct {
     int32_t lane_slot_triangles; /* capacity of the lane slot (0: no lane)          */
 } polylla_server_stats;
 
+/* The slots a server with these options would allocate (host arithmetic
+ * only: no CUDA call, usable without a GPU).  device_bytes is the server's
+ * own bound on what the slots hold (at most memory_budget); a slot holds at
+ * most 500 M triangles, so that its half-edge indices fit int32.  Errors:
+ * INVALID_ARGUMENT (NULL, a negative option, more than 16 copy-engine
+ * slots, or a budget too small for one triangle per slot). */
+typedef struct {
+    int32_t n_slots;             /* slots, the lane included                       */
+    int32_t slot_triangles;      /* capacity of one copy-engine slot               */
+    int32_t lane_triangles;      /* the lane's request limit (0: no lane)           */
+    int32_t lane_slot_triangles; /* capacity of the lane slot (0: no lane)          */
+    int64_t device_bytes;
+} polylla_server_plan;
+int polylla_server_plan_slots(const polylla_server_options *opt, polylla_server_plan *out);
+
 /* Create a server on the current device (allocates all slots; starts the
  * scheduler thread).  Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA. */
 int polylla_server_create(polylla_server **out, const polylla_server_options *opt);

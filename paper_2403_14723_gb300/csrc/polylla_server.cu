@@ -501,6 +501,46 @@ static void free_slot(Slot &s) {
     s = Slot();
 }
 
+// Slot capacities for a budget (host arithmetic only): the lane first,
+// kLaneBatch requests of its largest size within budget / (n + 1), then n
+// copy-engine slots splitting the rest; each capacity is the largest T
+// whose slot, with V <= T + 2m and H <= 4T + 2m for m meshes (bounds for
+// triangulated disks), fits its share.
+struct SlotPlan {
+    int n_ce = 0;
+    int64_t meshes = 0, T_ce = 0, T_lane = 0, lane_tri = 0, bytes = 0;
+};
+
+static int plan_slots(const polylla_server_options *opt, SlotPlan *p) {
+    if (!opt || opt->memory_budget <= 0 || opt->n_slots < 0 || opt->n_slots > kMaxCeSlots || opt->max_batch_meshes < 0 ||
+        opt->max_rotation < 0 || opt->max_batch_triangles < 0)
+        return POLYLLA_ERR_INVALID_ARGUMENT;
+    const int n_ce = opt->n_slots ? opt->n_slots : 3;
+    const int64_t m = opt->max_batch_meshes ? opt->max_batch_meshes : 4096;
+    const int64_t lane_req = opt->lane_triangles < 0 ? 0 : opt->lane_triangles ? opt->lane_triangles : kLaneDefault;
+    auto fit = [m](int64_t bytes, int64_t t_max) {
+        int64_t lo = 0, hi = t_max;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (slot_bytes(m, mid + 2 * m, mid, 4 * mid + 2 * m) <= bytes) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    auto bytes_of = [m](int64_t T) { return slot_bytes(m, T + 2 * m, T, 4 * T + 2 * m); };
+    const int64_t T_lane = lane_req > 0 ? fit(opt->memory_budget / (n_ce + 1), kLaneBatch * lane_req) : 0;
+    const int64_t lane_bytes = T_lane > 0 ? bytes_of(T_lane) : 0;
+    const int64_t T_ce = fit((opt->memory_budget - lane_bytes) / n_ce, 500000000);
+    if (T_ce < 1) return POLYLLA_ERR_INVALID_ARGUMENT;
+    p->n_ce = n_ce;
+    p->meshes = m;
+    p->T_ce = T_ce;
+    p->T_lane = T_lane;
+    p->lane_tri = T_lane > 0 ? std::min(lane_req, T_lane) : 0;
+    p->bytes = lane_bytes + n_ce * bytes_of(T_ce);
+    return POLYLLA_OK;
+}
+
 static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t T, int32_t H, bool lane) {
     s.n_cap = n;
     s.V_cap = V;
@@ -543,44 +583,22 @@ extern "C" {
 int polylla_server_create(polylla_server **out, const polylla_server_options *opt) {
     if (!out) return POLYLLA_ERR_INVALID_ARGUMENT;
     *out = nullptr;
-    if (!opt || opt->memory_budget <= 0 || opt->n_slots < 0 || opt->n_slots > kMaxCeSlots || opt->max_batch_meshes < 0 ||
-        opt->max_rotation < 0 || opt->max_batch_triangles < 0)
-        return POLYLLA_ERR_INVALID_ARGUMENT;
+    SlotPlan plan;
+    const int prc = plan_slots(opt, &plan);
+    if (prc) return prc;
     polylla_server *srv = new (std::nothrow) polylla_server();
     if (!srv) return POLYLLA_ERR_OUT_OF_MEMORY;
     if (cudaGetDevice(&srv->device) != cudaSuccess) {
         delete srv;
         return POLYLLA_ERR_CUDA;
     }
-    const int n_ce = opt->n_slots ? opt->n_slots : 3;
-    srv->max_batch = opt->max_batch_meshes ? opt->max_batch_meshes : 4096;
+    srv->max_batch = (int32_t)plan.meshes;
     srv->max_rotation = opt->max_rotation;
     srv->max_batch_tri = opt->max_batch_triangles;
-    const int64_t lane_req = opt->lane_triangles < 0 ? 0 : opt->lane_triangles ? opt->lane_triangles : kLaneDefault;
-    const int64_t n = srv->max_batch;
-    // slot capacity: the largest T (at most t_max) whose slot, with
-    // V <= T + 2n and H <= 4T + 2n (bounds for triangulated disks), fits bytes
-    auto fit = [n](int64_t bytes, int64_t t_max) {
-        int64_t lo = 0, hi = t_max;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) / 2;
-            if (slot_bytes(n, mid + 2 * n, mid, 4 * mid + 2 * n) <= bytes) lo = mid;
-            else hi = mid - 1;
-        }
-        return lo;
-    };
-    // the lane is one more, small slot: kLaneBatch requests of its largest
-    // size, within a share of the budget; the copy-engine slots split the rest
-    int64_t T_lane = lane_req > 0 ? fit(opt->memory_budget / (n_ce + 1), kLaneBatch * lane_req) : 0;
-    const int64_t lane_bytes = T_lane > 0 ? slot_bytes(n, T_lane + 2 * n, T_lane, 4 * T_lane + 2 * n) : 0;
-    const int64_t T_ce = fit((opt->memory_budget - lane_bytes) / n_ce, 500000000);
-    if (T_ce < 1) {
-        delete srv;
-        return POLYLLA_ERR_INVALID_ARGUMENT;
-    }
-    srv->lane_tri = T_lane > 0 ? (int32_t)std::min(lane_req, T_lane) : 0;
-    srv->n_slots = n_ce + (srv->lane_tri > 0 ? 1 : 0);
-    const int32_t T = (int32_t)T_ce, V = (int32_t)(T_ce + 2 * n), H = (int32_t)(4 * T_ce + 2 * n);
+    srv->lane_tri = (int32_t)plan.lane_tri;
+    srv->n_slots = plan.n_ce + (srv->lane_tri > 0 ? 1 : 0);
+    const int64_t n = plan.meshes, T_lane = plan.T_lane;
+    const int32_t T = (int32_t)plan.T_ce, V = (int32_t)(plan.T_ce + 2 * n), H = (int32_t)(4 * plan.T_ce + 2 * n);
     int rc = POLYLLA_OK;
     for (int k = 0; k < srv->n_slots && !rc; k++) {
         if (k == 0 && srv->lane_tri > 0)
@@ -606,6 +624,19 @@ int polylla_server_create(polylla_server **out, const polylla_server_options *op
     }
     srv->sched = std::thread([srv] { srv->loop(); });
     *out = srv;
+    return POLYLLA_OK;
+}
+
+int polylla_server_plan_slots(const polylla_server_options *opt, polylla_server_plan *out) {
+    if (!out) return POLYLLA_ERR_INVALID_ARGUMENT;
+    SlotPlan p;
+    const int rc = plan_slots(opt, &p);
+    if (rc) return rc;
+    out->n_slots = p.n_ce + (p.lane_tri > 0 ? 1 : 0);
+    out->slot_triangles = (int32_t)p.T_ce;
+    out->lane_triangles = (int32_t)p.lane_tri;
+    out->lane_slot_triangles = p.lane_tri > 0 ? (int32_t)p.T_lane : 0;
+    out->device_bytes = p.bytes;
     return POLYLLA_OK;
 }
 

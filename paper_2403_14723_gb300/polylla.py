@@ -111,6 +111,11 @@ class polylla_server_stats(ctypes.Structure):
                 ("lane_slot_triangles", ctypes.c_int32)]
 
 
+class polylla_server_plan(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("slot_triangles", ctypes.c_int32), ("lane_triangles", ctypes.c_int32),
+                ("lane_slot_triangles", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
 class polylla_batch_record(ctypes.Structure):
     _fields_ = [("t_form", ctypes.c_double), ("t_enqueued", ctypes.c_double), ("t_meta_seen", ctypes.c_double),
                 ("t_out_enqueued", ctypes.c_double), ("t_done", ctypes.c_double), ("in_ms", ctypes.c_float),
@@ -163,6 +168,8 @@ _SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(polylla_request_info)]),
     "polylla_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_server_stats)]),
+    "polylla_server_plan_slots": (ctypes.c_int, [ctypes.POINTER(polylla_server_options),
+                                                 ctypes.POINTER(polylla_server_plan)]),
     "polylla_server_get_batch_log": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(polylla_batch_record),
                                                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                                     ctypes.POINTER(ctypes.c_int64)]),
@@ -559,6 +566,16 @@ class HostRequest:
         return {"seeds": self.out["seeds"][:P].numpy().copy(), "offsets": self.out["offsets"][:P + 1].numpy().copy(),
                 "he_list": self.out["he_list"][:NF].numpy().copy(), "v_list": self.out["v_list"][:NF].numpy().copy(),
                 "next": self.out["next"].numpy().copy(), "prev": self.out["prev"].numpy().copy()}
+
+
+def server_plan(memory_budget: int, n_slots: int = 3, max_batch_meshes: int = 0, max_rotation: int = 0,
+                max_batch_triangles: int = 0, lane_triangles: int = 0) -> dict:
+    """The slots a Server with these options would allocate (no GPU needed)."""
+    opt = polylla_server_options(int(memory_budget), int(n_slots), int(max_batch_meshes), int(max_rotation),
+                                 int(max_batch_triangles), int(lane_triangles))
+    out = polylla_server_plan()
+    _check(load_library().polylla_server_plan_slots(ctypes.byref(opt), ctypes.byref(out)), "polylla_server_plan_slots")
+    return {k: getattr(out, k) for k, _ in polylla_server_plan._fields_}
 
 
 def _info_dict(info: polylla_request_info) -> dict:
