@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["polylla_api.cu", "kernels_label.cu", "kernels_repair.cu", "kernels_output.cu", "kernels_batch.cu",
            "kernels_serve.cu", "polylla_noalloc.cu", "polylla_server.cu", "kernels_lepp.cu"]
-HEADERS = [os.path.join(CSRC, "polylla_internal.cuh"), os.path.join(CSRC, "polylla_serve.cuh"), os.path.join(INCLUDE, "polylla.h")]
+HEADERS = [os.path.join(CSRC, "polylla_internal.cuh"), os.path.join(CSRC, "polylla_serve.cuh"),
+           os.path.join(CSRC, "serve_policy.h"), os.path.join(INCLUDE, "polylla.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]

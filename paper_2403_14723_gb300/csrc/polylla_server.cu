@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "polylla_serve.cuh"
+#include "serve_policy.h"
 
 using namespace polylla;
 
@@ -198,40 +199,21 @@ bool polylla_server::launch(Slot &s) {
     std::vector<Req *> take;
     {
         std::lock_guard<std::mutex> g(mu);
-        int64_t V = 0, T = 0, H = 0;
-        const double t_now = now();
-        const int32_t cap_n = std::min(s.n_cap, max_batch);
-        for (auto it = pending.begin(); it != pending.end() && (int32_t)take.size() < cap_n;) {
-            Req *q = *it;
-            const polylla_request &r = q->r;
-            const bool small = lane_tri > 0 && lane_ok(q);
-            if (lane_tri > 0 && s.lane != small && (s.lane || t_now - q->t_submit < kStealSeconds)) {
-                ++it;  // the lane takes lane requests only; the others leave them to it for a while
-                continue;
-            }
-            if (r.n_vertices > s.V_cap || r.n_triangles > s.T_cap || r.n_halfedges > s.H_cap) {
-                if (small) {
-                    ++it;  // fits the lane (checked by lane_ok), not this slot
-                    continue;
-                }
-                // larger than any slot (the copy-engine slots are identical and
-                // the largest): fails now
-                it = pending.erase(it);
-                q->status = POLYLLA_ERR_TOO_LARGE;
-                q->t_admit = q->t_done = now();
-                q->done = true;
-                done_count++;
-                cv_done.notify_all();
-                continue;
-            }
-            if (V + r.n_vertices > s.V_cap || T + r.n_triangles > s.T_cap || H + r.n_halfedges > s.H_cap) break;
-            if (!take.empty() && max_batch_tri > 0 && T + r.n_triangles > max_batch_tri) break;
-            V += r.n_vertices;
-            T += r.n_triangles;
-            H += r.n_halfedges;
-            take.push_back(q);
-            it = pending.erase(it);
-        }
+        const policy::SlotView sv{s.V_cap, s.T_cap, s.H_cap, std::min(s.n_cap, max_batch), s.lane};
+        auto view = [this](Req *q) {
+            return policy::ReqView{q->r.n_vertices, q->r.n_triangles, q->r.n_halfedges, lane_tri > 0 && lane_ok(q),
+                                   q->t_submit};
+        };
+        // larger than any slot (the copy-engine slots are identical and the
+        // largest) and not a lane request: fails now
+        auto fail = [this](Req *q) {
+            q->status = POLYLLA_ERR_TOO_LARGE;
+            q->t_admit = q->t_done = now();
+            q->done = true;
+            done_count++;
+            cv_done.notify_all();
+        };
+        policy::form_batch(pending, sv, lane_tri > 0, now(), kStealSeconds, max_batch_tri, view, fail, take);
     }
     if (take.empty()) return false;
     const int32_t n = (int32_t)take.size();
