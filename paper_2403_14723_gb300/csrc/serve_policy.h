@@ -31,7 +31,7 @@ struct SlotView {
     bool lane;         // the low-latency lane
 };
 
-enum class Verdict { Take, Skip, Fail, Stop };
+enum class Decision { Take, Skip, Fail, Stop };
 
 struct BatchSoFar {
     int64_t V = 0, T = 0, H = 0;
@@ -39,15 +39,15 @@ struct BatchSoFar {
 };
 
 // What a forming batch on slot s does with request r at time now.
-inline Verdict admit(const ReqView &r, const SlotView &s, bool lane_on, double now, double steal_s,
+inline Decision admit(const ReqView &r, const SlotView &s, bool lane_on, double now, double steal_s,
                      int64_t max_batch_tri, const BatchSoFar &b) {
     if (lane_on && s.lane != r.small && (s.lane || now - r.t_submit < steal_s))
-        return Verdict::Skip;  // the lane takes lane requests only; the others leave them to it for a while
+        return Decision::Skip;  // the lane takes lane requests only; the others leave them to it for a while
     if (r.V > s.V_cap || r.T > s.T_cap || r.H > s.H_cap)
-        return r.small ? Verdict::Skip : Verdict::Fail;  // a lane request may still fit the lane
-    if (b.V + r.V > s.V_cap || b.T + r.T > s.T_cap || b.H + r.H > s.H_cap) return Verdict::Stop;
-    if (b.n > 0 && max_batch_tri > 0 && b.T + r.T > max_batch_tri) return Verdict::Stop;
-    return Verdict::Take;
+        return r.small ? Decision::Skip : Decision::Fail;  // a lane request may still fit the lane
+    if (b.V + r.V > s.V_cap || b.T + r.T > s.T_cap || b.H + r.H > s.H_cap) return Decision::Stop;
+    if (b.n > 0 && max_batch_tri > 0 && b.T + r.T > max_batch_tri) return Decision::Stop;
+    return Decision::Take;
 }
 
 // Form one batch for slot s from the queue: taken requests move to take
@@ -60,7 +60,7 @@ void form_batch(std::deque<Q> &pending, const SlotView &s, bool lane_on, double 
     for (auto it = pending.begin(); it != pending.end() && b.n < s.n_cap;) {
         const ReqView r = view(*it);
         switch (admit(r, s, lane_on, now, steal_s, max_batch_tri, b)) {
-        case Verdict::Take:
+        case Decision::Take:
             b.V += r.V;
             b.T += r.T;
             b.H += r.H;
@@ -68,14 +68,14 @@ void form_batch(std::deque<Q> &pending, const SlotView &s, bool lane_on, double 
             take.push_back(*it);
             it = pending.erase(it);
             break;
-        case Verdict::Skip:
+        case Decision::Skip:
             ++it;
             break;
-        case Verdict::Fail:
+        case Decision::Fail:
             on_fail(*it);
             it = pending.erase(it);
             break;
-        case Verdict::Stop:
+        case Decision::Stop:
             return;
         }
     }
