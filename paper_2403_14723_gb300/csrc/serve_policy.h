@@ -40,7 +40,7 @@ struct BatchSoFar {
 
 // What a forming batch on slot s does with request r at time now.
 inline Decision admit(const ReqView &r, const SlotView &s, bool lane_on, double now, double steal_s,
-                     int64_t max_batch_tri, const BatchSoFar &b) {
+                      int64_t max_batch_tri, const BatchSoFar &b) {
     if (lane_on && s.lane != r.small && (s.lane || now - r.t_submit < steal_s))
         return Decision::Skip;  // the lane takes lane requests only; the others leave them to it for a while
     if (r.V > s.V_cap || r.T > s.T_cap || r.H > s.H_cap)
