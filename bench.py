@@ -245,7 +245,7 @@ def algorithmic_bytes(T, V, NF, P):
 
 def ref_sample_mesh(workload: str, runs: int = 3):
     """A bounded sample of the workload for the oracle: about 10-30 s of
-    single-threaded CPU work over ``runs`` runs on the GPU machine's cores."""
+    single-threaded CPU work over ``runs`` runs on the host cores beside the GPU."""
     from paper_2403_14723_gb300 import meshgen
 
     if workload == "served":
