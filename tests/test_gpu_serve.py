@@ -71,6 +71,9 @@ def test_served_requests_match_oracle_alone_and_in_the_mix():
         # small pinned requests ran in the lane (kernel copies), the large one outside it
         assert st["lane_triangles"] == 65536 and st["lane_batches"] >= 1
         assert st["n_slots"] == 4 and st["lane_slot_triangles"] >= 65536    # three copy-engine slots and the lane
+        plan = polylla.server_plan(3 << 30, n_slots=3, max_batch_meshes=16)   # the same options, no GPU
+        for k in ("n_slots", "slot_triangles", "lane_triangles", "lane_slot_triangles"):
+            assert st[k] == plan[k], k
         assert any(b["lane"] == 1 for b in log) and any(b["lane"] == 0 for b in log)
         assert st["launches"] == 19 * st["lane_batches"] + 18 * (st["batches"] - st["lane_batches"])
 
