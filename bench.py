@@ -217,25 +217,26 @@ def ncu_traffic(kernel: str):
 def algorithmic_bytes(T, V, NF, P):
     """Bytes the method must move once, B_alg = 24T + 16V + 16 N_F + 8P
     (next/prev of interior half-edges are implicit in the layout; label
-    bytes are L2-resident and not counted), and per kernel the bytes that
-    kernel must move for its own job (its unique inputs and outputs; the
-    output kernels re-read next, so the per-kernel figures sum to more
-    than B_alg)."""
+    bytes are L2-resident and not counted), and each kernel's share of it:
+    the longest edge reads origin and coords (12T + 16V), the relink reads
+    twin and writes next/prev of the frontier (12T + 8 N_F), the listing
+    kernel writes the CSR (8 N_F + 8P); the repair kernels, the polygon
+    count (a second read of next) and the batch format kernels move no
+    bytes of B_alg.  The shares sum to B_alg, so a
+    kernel's traffic over its share is the bytes it re-reads."""
     total = 24 * T + 16 * V + 16 * NF + 8 * P
     per_stage = {
-        "longest_edge": 12 * T + 16 * V + T,        # origin, coords; le out
-        "label_relink": 12 * T + T + 8 * NF + T,    # twin, le; next/prev of frontier, flags out
+        "longest_edge": 12 * T + 16 * V,
+        "label_relink": 12 * T + 8 * NF,
         "chords": 0,
         "chord_links": 0,
-        "cand_count": T,                             # flags
-        "cand_scan": 0,
-        "cand_write": T,                             # flags (starts out: ~P ints, not counted)
-        "walk": 4 * NF,                              # next of every frontier half-edge once
-        "chunk_scan": 0,
-        "emit": 4 * NF + 4 * NF + 8 * NF + 8 * P,    # next, origin; CSR out
-        "batch_pack": 0,                             # batches only
+        "poly_count": 0,
+        "tile_scan": 0,
+        "poly_list": 8 * NF + 8 * P,
+        "batch_pack": 0,
         "batch_unpack": 0,
     }
+    assert sum(per_stage.values()) == total
     return total, per_stage
 
 
@@ -397,14 +398,25 @@ def run_gb300(args):
     dominant = max(stage_ms, key=stage_ms.get)
     peak, peak_kind = measured_peaks()
     ach = per_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+    traffic = ncu_traffic(dominant)
+    kernels = {}
+    for k, t_ms in stage_ms.items():
+        if t_ms <= 0.0:
+            continue
+        share = per_stage.get(k, 0)
+        tr = ncu_traffic(k)
+        kernels[k] = {"ms": t_ms, "share_bytes": share,
+                      "frac": (share / (t_ms * 1e-3) / 1e9 / peak) if share else None,
+                      "traffic": tr, "traffic_over_share": (tr / share) if (tr and share) else None}
     roofline = {
+        "whole_step": {"algorithmic_bytes": total_alg, "achieved": total_alg / (ms * 1e-3) / 1e9,
+                       "frac": total_alg / (ms * 1e-3) / 1e9 / peak, "ms": ms},
         "bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "unit": "GB/s",
         "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs",
-        "traffic": ncu_traffic(dominant),
+        "traffic": traffic,
         "algorithmic_bytes": per_stage[dominant],
         "stage_ms": stage_ms,
-        "whole_step": {"algorithmic_bytes": total_alg, "achieved": total_alg / (ms * 1e-3) / 1e9,
-                       "frac": total_alg / (ms * 1e-3) / 1e9 / peak},
+        "kernels": kernels,
     }
 
     # ---- the Lepp primitive over the same mesh (after a generate) ---------
@@ -592,7 +604,7 @@ def run_batched(args):
             ms = timed(args.steps, step)
         dist_barrier(ws)
         ms = dist_max(ms, ws)
-        launches = args.steps * 15
+        launches = args.steps * polylla.polylla_launch_count(ctx)
         out = polylla.polylla_get_polygons(ctx, stream)
         P, NF = out["n_polygons"], out["n_frontier"]
         po = polylla.polylla_batch_polygon_offsets(ctx, n_meshes).cpu().numpy()

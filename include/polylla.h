@@ -47,7 +47,8 @@ enum polylla_status {
     POLYLLA_ERR_NONTERMINATING = -5,   /* a rotation or cycle walk hit its cap       */
     POLYLLA_ERR_CAPACITY = -6,         /* an internal list overflowed its capacity   */
     POLYLLA_ERR_TIMEOUT = -7,          /* a device wait gave up                      */
-    POLYLLA_ERR_TOO_LARGE = -8,        /* mesh exceeds polylla_generate_noalloc's scratch */
+    POLYLLA_ERR_TOO_LARGE = -8,        /* mesh larger than the capacity available:    */
+                                       /* the no-allocation scratch, or a server slot */
 };
 
 /* Input mesh (device arrays owned by the caller). */
@@ -213,10 +214,12 @@ int polylla_generate_host(polylla_ctx *ctx, const polylla_host_mesh *in,
  * n stages of the last generate (0 for a stage that did not run: the two
  * batch stages on a single mesh), returning how many it wrote, or 0 when
  * the last generate was not timed (timing off, or a captured graph).
- * polylla_stage_name gives the name of stage i: the ten stages of the
- * method, then "batch_pack" and "batch_unpack".
- * polylla_launch_count gives the number of kernels the last generate
- * launched (10 for a mesh, 15 for a batch).
+ * polylla_stage_name gives the name of stage i: the seven kernels of the
+ * method ("longest_edge", "label_relink", "chords", "chord_links",
+ * "poly_count", "tile_scan", "poly_list"), then "batch_pack" and
+ * "batch_unpack".  polylla_launch_count gives the number of kernels the
+ * last generate launched (7 for a mesh, 12 for a batch, 13 for a served
+ * batch).
  */
 int polylla_set_timing(polylla_ctx *ctx, int32_t enable);
 int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
@@ -270,7 +273,7 @@ int polylla_batch_polygon_offsets(polylla_ctx *ctx, const int32_t **poly_offset)
  * context (its kernels, with the current launch settings) into a CUDA graph
  * on stream (which must not be NULL, the legacy stream cannot be captured);
  * from then on polylla_generate launches that graph, one launch instead of
- * 10 or 15, untimed.  Changing the launch settings (polylla_set_tuning,
+ * 7 or 12, untimed.  Changing the launch settings (polylla_set_tuning,
  * polylla_autotune) or polylla_release_graph drops the graph.  The graph
  * reads and writes the same device arrays as the captured generate.
  */
@@ -279,22 +282,25 @@ int polylla_release_graph(polylla_ctx *ctx);
 
 /*
  * Launch tuning (results never depend on it).  relink_threads is the block
- * size of the relink kernel (64, 128 or 256); the others are the grid sizes
- * (blocks) of the persistent longest-edge, walk and emit kernels, each in
- * [1, 64 * SMs].  polylla_autotune times whole generates (reps per setting,
- * median of the stage's CUDA-event time), tries the candidates of one
- * setting at a time in stage order and keeps the fastest, applies the
- * result to the context, stores it in a process-wide table per device and
- * size bucket (floor(log2 T), T the mesh's or batch's triangle count) that
- * contexts created later start from, and writes it to *out (may be NULL).
- * It runs generate on the context's mesh (idempotent) and synchronizes
- * stream.  polylla_tuning_cache_clear empties the table.
+ * size of the relink kernel (64, 128 or 256); longest_edge_blocks the grid
+ * (blocks, in [1, 64 * SMs]) of the persistent longest-edge kernel;
+ * output_tile the triangles per tile of the output kernel (1024, 2048 or
+ * 4096) and output_items the triangles each of its threads walks and lists
+ * (4 or 8; a tile of 4096 with 4 per thread is a block of 1024 threads).
+ * polylla_autotune times whole generates (reps per setting, median of the
+ * stage's CUDA-event time), tries the candidates of one setting at a time in
+ * stage order and keeps the fastest, applies the result to the context,
+ * stores it in a process-wide table per device and size bucket
+ * (floor(log2 T), T the mesh's or batch's triangle count) that contexts
+ * created later start from, and writes it to *out (may be NULL).  It runs
+ * generate on the context's mesh (idempotent) and synchronizes stream.
+ * polylla_tuning_cache_clear empties the table.
  */
 typedef struct {
     int32_t relink_threads;
     int32_t longest_edge_blocks;
-    int32_t walk_blocks;
-    int32_t emit_blocks;
+    int32_t output_tile;
+    int32_t output_items;
 } polylla_tuning;
 int polylla_get_tuning(polylla_ctx *ctx, polylla_tuning *out);
 int polylla_set_tuning(polylla_ctx *ctx, const polylla_tuning *tuning);
@@ -488,13 +494,14 @@ void polylla_server_destroy(polylla_server *srv);
  * polylla_generate_noalloc -- the whole method, allocating nothing.
  *
  * (No counterpart in the paper: this is a deployment convenience.)  For
- * callers that cannot call cudaMalloc -- a serving loop that must not
- * allocate once running, code recorded into a CUDA graph, or a process
- * whose device memory belongs to another allocator.  It runs the same
- * kernels as polylla_generate, but their scratch (labels, tip lists, tile
- * totals, polygon minima, counters) lives in one static device array of
+ * callers that cannot call cudaMalloc: a serving loop that must not
+ * allocate once it runs (an allocation can block on, or fail against,
+ * memory other work holds), or a process whose device memory belongs to
+ * another allocator that a stray cudaMalloc would fragment or bypass.  It
+ * runs the same kernels as polylla_generate, but their scratch (labels, tip
+ * lists, output tile words, counters) lives in one static device array of
  * fixed size that every GPU loading the library holds until the process
- * exits (about 4.5 MB), so no context, no cudaMalloc and no cudaFree.
+ * exits (about 1.7 MB), so no context, no cudaMalloc and no cudaFree.
  *
  *   mesh    device arrays as for polylla_create; must satisfy the layout
  *           polylla_create checks (no check is made here);
@@ -507,8 +514,10 @@ void polylla_server_destroy(polylla_server *srv);
  *   stream  everything is enqueued on it; the call does not synchronize.
  * Returns POLYLLA_ERR_TOO_LARGE (nothing launched) when T exceeds
  * POLYLLA_NOALLOC_MAX_TRIANGLES or V exceeds it by more than 2,
- * POLYLLA_ERR_INVALID_ARGUMENT for NULL or misaligned pointers, otherwise
- * POLYLLA_OK or POLYLLA_ERR_CUDA.
+ * POLYLLA_ERR_INVALID_ARGUMENT for NULL or misaligned pointers,
+ * POLYLLA_ERR_CUDA (nothing launched, the error left pending for the caller)
+ * when a CUDA error of earlier work is already pending on the calling
+ * thread, otherwise POLYLLA_OK or POLYLLA_ERR_CUDA.
  *
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -171,8 +171,10 @@ __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w)
     __shared__ __align__(128) int32_t s_org[NW][2][3 * LE_TILE];
     __shared__ __align__(8) uint64_t s_bar[NW][2];
     // reset this generate's control block (error word, tip count, totals)
+    // and the output tiles' totals
     const int32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gtid < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[gtid] = 0;
+    for (int32_t i = gtid; i < w.n_tile_max; i += gridDim.x * blockDim.x) w.tile_state[i] = 0ull;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;

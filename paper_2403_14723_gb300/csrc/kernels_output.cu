@@ -1,30 +1,32 @@
-// Output kernels (stages 5b-5d): find every polygon, key it by its smallest
-// half-edge, and write the scan-compacted CSR in ascending seed order.
+// Output kernel (stages 5b-5d): find every polygon, key it by its smallest
+// half-edge, and write the scan-compacted CSR in ascending seed order, in
+// one launch.
 //
 // A frontier half-edge e is its polygon's minimum iff walking next from e
 // comes back to e without meeting a smaller half-edge.  A minimum is smaller
 // than both its neighbours along the polygon, so only half-edges carrying
 // the relink's walk-start mark (next and prev both larger, a superset kept
-// by the repair) walk; polygons are listed in an order that rises and then
-// falls, so that is about one walk per polygon on the workloads measured.
-// This finds every cycle of the relink exactly once, keyed by the canonical
-// seed the paper's Algorithm 14 keeps, without a seed list.
+// by the repair) walk.  This finds every cycle of the relink exactly once,
+// keyed by the canonical seed the paper's Algorithm 14 keeps, without a seed
+// list; listing each minimum's cycle from the minimum, minima in ascending
+// order, is the canonical CSR (Section 6.8's scan-and-compact output).
 //
-// The walks are chains of dependent loads, so the kernels are organised
-// for the largest number of chains in flight and no block ever waits for
-// the slowest walk of its tile:
-//   k_cand_count  marks per block of 16384 triangles        (flags, int4 loads)
-//   k_scan_blocks exclusive scan of those counts            (one block)
-//   k_cand_write  the walk starts, in index order           (scan-compaction)
-//   k_walk        one chain per lane, grid-stride, two chains interleaved;
-//                 (polygon count, length) per 32 starts, and per
-//                 2048-start chunk by per-warp atomics
-//   k_scan_blocks exclusive scan of the chunk totals -> P, N_F, offsets[P]
-//   k_emit        per warp and 64 starts: offsets by warp scan over the
-//                 chunk prefix and the group totals before it; every
-//                 minimum writes its seed and offset and lists its polygon
-//                 (two interleaved per lane) through a per-warp shared
-//                 buffer that goes out with coalesced stores.
+// The stage works on tiles of consecutive triangles.  Meshes come in a
+// spatially coherent order, so about nine polygons in ten lie inside the
+// tile that holds their minimum, and two kernels stream the tiles through
+// shared memory (bulk copies by the TMA engine, one mbarrier per CTA):
+//   k_poly_count  walks the starts of its tile (leaving the tile only for
+//                 the polygons that cross it) and totals the minima's
+//                 (count, length) pairs per warp and per tile;
+//   k_tile_scan   scans the tile totals (one block);
+//   k_poly_list   lists every warp's polygons through a staging buffer
+//                 that goes out with coalesced stores.
+// No warp waits for another warp.  Two designs that did were slower: a
+// single kernel whose tiles looked back for the totals of tiles still being
+// walked (every CTA in flight waited for the slowest walk before it), and a
+// listing kernel whose tiles looked back for the prefixes of tiles still
+// being listed (each look-back summed back over the tiles started during
+// its own round trip to L2).
 #include "polylla_internal.cuh"
 
 namespace polylla {
@@ -68,58 +70,14 @@ __device__ unsigned long long block_excl_scan(unsigned long long v, unsigned lon
     return wb + inc - v;
 }
 
-// The walk starts of 16 triangles t0 .. t0+15 as four words: byte q of
-// word i holds the start bits of triangle t0 + 4i + q in its low 3 bits
-// (a start is frontier and marked: f & (f >> 3) & 7 per flags byte, done
-// on four bytes at once; bits shifted in from the next byte are masked).
-// flags is allocated to a multiple of 16 bytes: the int4 stays in bounds.
-__device__ __forceinline__ void start_words(const MeshView &m, const Work &w, int32_t t0, uint32_t st[4]) {
-    st[0] = st[1] = st[2] = st[3] = 0u;
-    if (t0 >= m.T) return;
-    const int4 v = *reinterpret_cast<const int4 *>(w.flags + t0);
-    const uint32_t wd[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
-#pragma unroll
-    for (int i = 0; i < 4; i++) st[i] = wd[i] & (wd[i] >> 3) & 0x07070707u;
-    const int32_t valid = m.T - t0;  // triangles of the 16 inside [0, T)
-    if (valid < 16) {
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int32_t keep = valid - 4 * i;  // bytes of word i to keep
-            if (keep <= 0) st[i] = 0u;
-            else if (keep < 4) st[i] &= (1u << (8 * keep)) - 1u;
-        }
-    }
-}
-
 // ===========================================================================
-// k_cand_count: walk starts per block of CC_TRI triangles; also zeroes the
-// chunk totals the walk kernel accumulates into.
-// ===========================================================================
-__global__ void __launch_bounds__(CC_THREADS) k_cand_count(MeshView m, Work w) {
-    __shared__ unsigned long long s_warp[33];
-    const int32_t gtid = blockIdx.x * CC_THREADS + threadIdx.x;
-    for (int32_t i = gtid; i < w.n_chunk_max; i += gridDim.x * CC_THREADS) w.blk_b[i] = 0ull;
-    const int32_t t0 = blockIdx.x * CC_TRI + threadIdx.x * CC_PER;  // 16 triangles per thread
-    uint32_t st[4];
-    start_words(m, w, t0, st);
-    const uint32_t c = __popc(st[0]) + __popc(st[1]) + __popc(st[2]) + __popc(st[3]);
-    unsigned long long total;
-    block_excl_scan(c, s_warp, &total);
-    if (threadIdx.x == 0) w.blk_a[blockIdx.x] = total;
-}
-
-// ===========================================================================
-// k_scan_blocks: one block, exclusive scan of n (read from *n_dev when n < 0)
-// 64-bit totals; *grand receives the sum.  Rounds of blockDim.x coalesced
-// entries with a running carry.  With finish set (the chunk totals), thread
-// 0 then turns the grand total into P, N_F and offsets[P].
+// k_scan_blocks: one block, exclusive scan of n 64-bit values; *grand
+// receives the sum.  Rounds of blockDim.x coalesced entries with a running
+// carry.  (Used by the Lepp paths.)
 // ===========================================================================
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned long long *in, unsigned long long *out,
-                                                              int32_t n, const int32_t *n_dev, int32_t n_max,
-                                                              unsigned long long *grand, MeshView m, Work w,
-                                                              int finish) {
+                                                              int32_t n, unsigned long long *grand) {
     __shared__ unsigned long long s_warp[33];
-    if (n < 0) n = min(*n_dev, n_max);
     unsigned long long carry = 0;
     for (int32_t b = 0; b < n; b += SCAN_THREADS) {
         const int32_t i = b + threadIdx.x;
@@ -129,275 +87,330 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const unsigned lon
         if (i < n) out[i] = carry + ex;
         carry += total;
     }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+void launch_scan_u64(const unsigned long long *in, unsigned long long *out, int32_t n, unsigned long long *grand,
+                     cudaStream_t s) {
+    k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(in, out, n, grand);
+}
+
+// ---- tiles -----------------------------------------------------------------
+// A tile is TILE consecutive triangles (3 TILE half-edges); its copies start
+// on 16-byte boundaries (TILE is a multiple of 16) and round their length up
+// to 16 bytes: at most 3 ints past 3T, inside next/origin because
+// H >= 3T + 3, and flags is allocated to a multiple of 16 bytes.
+__device__ __forceinline__ uint32_t tile_bytes(int32_t nt, int32_t bytes_per_triangle) {
+    return ((uint32_t)(bytes_per_triangle * nt) + 15u) & ~15u;
+}
+
+// ===========================================================================
+// k_poly_count<TILE, NT>: one CTA per tile, TILE / NT consecutive triangles
+// per thread.  Thread 0 bulk-copies the tile's next and flags into shared
+// memory; every start of the thread's triangles walks next (shared memory
+// inside the tile, global memory outside) until a smaller half-edge or back
+// to itself.  A warp scan of the minima's (count, length) pairs gives each
+// thread its place in its warp's range; each warp stores its total and adds
+// it to the tile's total (zeroed by the first kernel of the generate).  No
+// warp waits for another: a slow walk holds up its own warp only.
+// ===========================================================================
+template <int TILE, int NT>
+__global__ void __launch_bounds__(NT) k_poly_count(MeshView m, Work w) {
+    constexpr int IPT = TILE / NT;
+    constexpr int E = 3 * TILE;
+    constexpr int NW = NT / 32;
+    static_assert(TILE % NT == 0 && IPT >= 1 && 3 * IPT <= 32, "a thread's half-edges fit one 32-bit mask");
+    static_assert(TILE % 16 == 0, "tile copies start on 16-byte boundaries");
+    extern __shared__ __align__(128) unsigned char smem[];
+    int32_t *s_nx = reinterpret_cast<int32_t *>(smem);         // [E]
+    uint8_t *s_fl = reinterpret_cast<uint8_t *>(s_nx + E);     // [TILE]
+    __shared__ __align__(8) uint64_t s_bar;
+    const int32_t HI = 3 * m.T;
+    const int32_t tile = blockIdx.x;
+    const int32_t t0 = tile * TILE;
+    const int32_t nt = min(TILE, m.T - t0);
+    const int32_t eb = 3 * t0;
+    const uint32_t ne = (uint32_t)(3 * nt);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t rec = (int64_t)tile * NT + threadIdx.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+        const uint32_t be = tile_bytes(nt, 12), bf = tile_bytes(nt, 1);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar, be + bf);
+        bulk_load(s_nx, m.next + eb, be, &s_bar);
+        bulk_load(s_fl, w.flags + t0, bf, &s_bar);
+    }
+    __syncthreads();
+    const bool loaded = __all_sync(0xffffffffu, mbar_wait(&s_bar, 0));
+    uint32_t minmask = 0, cnt = 0, len = 0;
+    if (loaded) {
+        const int32_t lt0 = (int32_t)threadIdx.x * IPT;
+        bool runaway = false;
+#pragma unroll
+        for (int q = 0; q < IPT; q++) {
+            const int32_t lt = lt0 + q;
+            if (lt >= nt) break;
+            const uint32_t f = s_fl[lt];
+            uint32_t st = f & (f >> 3) & 7u;
+            while (st) {
+                const int k = __ffs(st) - 1;
+                st &= st - 1u;
+                const int32_t e = eb + 3 * lt + k;
+                int32_t x = s_nx[3 * lt + k];
+                uint32_t L = 1;
+                while (x > e) {
+                    const uint32_t d = (uint32_t)(x - eb);
+                    x = d < ne ? s_nx[d] : __ldg(m.next + x);
+                    if (++L > (uint32_t)HI) {
+                        runaway = true;
+                        x = -1;
+                    }
+                }
+                if (x == e) {
+                    minmask |= 1u << (3 * q + k);
+                    cnt++;
+                    len += L;
+                }
+            }
+        }
+        if (runaway) atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
+    } else if (lane == 0) {
+        // copies not seen in time: record it; this warp's part of the tile
+        // stays empty
+        atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
+    }
+    const unsigned long long v = ((unsigned long long)cnt << 32) | len;
+    const unsigned long long inc = warp_incl_scan(v, lane);
+    w.poly_rec[rec] = inc - v;
+    w.poly_min[rec] = minmask;
+    if (lane == 31) {
+        w.poly_wtot[(int64_t)tile * NW + wid] = inc;
+        atomicAdd(w.tile_state + tile, inc);
+    }
+    // a CTA leaves only after its bulk copies landed (bounded wait)
+    if (!loaded && threadIdx.x == 0) mbar_wait(&s_bar, 0);
+}
+
+// ===========================================================================
+// k_tile_scan: one block, exclusive scan of the tiles' (polygons, length)
+// totals into tile_pre; thread 0 then writes P, N_F and offsets[P] and
+// checks the capacities.
+// ===========================================================================
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(MeshView m, Work w, int32_t n) {
+    __shared__ unsigned long long s_warp[33];
+    unsigned long long carry = 0;
+    for (int32_t b = 0; b < n; b += SCAN_THREADS) {
+        const int32_t i = b + threadIdx.x;
+        const unsigned long long v = i < n ? w.tile_state[i] : 0ull;
+        unsigned long long total;
+        const unsigned long long ex = block_excl_scan(v, s_warp, &total);
+        if (i < n) w.tile_pre[i] = carry + ex;
+        carry += total;
+    }
     if (threadIdx.x != 0) return;
-    *grand = carry;
-    if (!finish) return;
-    int32_t P = (int32_t)(carry >> 32);
-    const int64_t NF = (int64_t)(carry & 0xffffffffu);
-    if (P > m.T || NF > 3 * (int64_t)m.T) {
+    int64_t P = (int64_t)(carry >> 32);
+    const int64_t NF = (int64_t)(carry & 0xffffffffull);
+    if (P > (int64_t)m.T || NF > 3 * (int64_t)m.T) {
         atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
         P = P > m.T ? m.T : P;
     }
     w.offsets[P] = (int32_t)NF;
-    w.ctrl->n_polygons = P;
+    w.ctrl->n_polygons = (int32_t)P;
     w.ctrl->n_frontier = (int32_t)NF;
     if (w.input_err && *w.input_err) atomicOr(&w.ctrl->error, DEV_ERR_INPUT);
 }
 
 // ===========================================================================
-// k_cand_write: the walk starts of each block, in index order, at the
-// block's scanned offset, staged in shared memory and stored coalesced.  Also stores the start count and the number of
-// 2048-start chunks for the kernels that follow.
+// k_poly_list<TILE, NT>: one CTA per tile.  Thread 0 bulk-copies the tile's
+// next and origin.  Then every warp works on its own: its first polygon and
+// entry are the scanned total of the tiles before its tile plus the totals
+// of the warps before it in the tile; every minimum of its lanes writes its
+// seed and offset and lists its polygon from itself along next (half-edge
+// and its origin) into the warp's staging buffer (entries past it go out
+// directly), which the warp then stores, one contiguous range of he_list
+// and v_list, coalesced.
 // ===========================================================================
-__global__ void __launch_bounds__(CC_THREADS) k_cand_write(MeshView m, Work w) {
-    __shared__ unsigned long long s_warp[33];
-    __shared__ __align__(16) int32_t s_out[CW_BUF];
-    const int32_t t0 = blockIdx.x * CC_TRI + threadIdx.x * CC_PER;
-    uint32_t st[4];
-    start_words(m, w, t0, st);
-    const uint32_t c = __popc(st[0]) + __popc(st[1]) + __popc(st[2]) + __popc(st[3]);
-    unsigned long long total;
-    const int32_t ex = (int32_t)block_excl_scan(c, s_warp, &total);
-    const int64_t base = (int64_t)w.blk_a_pre[blockIdx.x];
-    const int32_t cap = 3 * m.T;
-    // the block's starts go to shared memory in order, then out with
-    // coalesced stores; any past the buffer (more than CW_BUF starts in one
-    // block, not seen on the workloads measured) go out directly
-    int32_t k = ex;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        uint32_t bits = st[i];
-        while (bits) {
-            const int b = __ffs(bits) - 1;  // byte q = b / 8 (triangle t0 + 4i + q), corner k = b % 8
-            bits &= bits - 1u;
-            const int32_t e = 3 * (t0 + 4 * i + (b >> 3)) + (b & 7);
-            if (k < CW_BUF) s_out[k] = e;
-            else if (base + k < cap) w.cand[base + k] = e;
-            k++;
-        }
+template <int TILE, int NT>
+__global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
+    constexpr int IPT = TILE / NT;
+    constexpr int E = 3 * TILE;
+    constexpr int NW = NT / 32;
+    constexpr int WCAP = 64 * IPT;  // CSR entries a warp stages
+    extern __shared__ __align__(128) unsigned char smem[];
+    int32_t *s_nx = reinterpret_cast<int32_t *>(smem);  // [E]
+    int32_t *s_org = s_nx + E;                          // [E]
+    int32_t *s_stage = s_org + E;                       // [NW][2][WCAP]
+    __shared__ __align__(8) uint64_t s_bar;
+    const int32_t HI = 3 * m.T;
+    const int32_t tile = blockIdx.x;
+    const int32_t t0 = tile * TILE;
+    const int32_t nt = min(TILE, m.T - t0);
+    const int32_t eb = 3 * t0;
+    const uint32_t ne = (uint32_t)(3 * nt);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+        const uint32_t be = tile_bytes(nt, 12);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar, 2 * be);
+        bulk_load(s_nx, m.next + eb, be, &s_bar);
+        bulk_load(s_org, m.origin + eb, be, &s_bar);
     }
     __syncthreads();
-    const int32_t nb = min((int32_t)total, CW_BUF);
-    for (int32_t i = threadIdx.x; i < nb; i += CC_THREADS)
-        if (base + i < cap) w.cand[base + i] = s_out[i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int64_t nc = (int64_t)w.ctrl->n_cand64;  // written by the scan of the block counts
-        if (nc > cap) {
-            atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
-            nc = cap;
-        }
-        w.ctrl->n_cand = (int32_t)nc;
-        w.ctrl->n_chunks = (int32_t)((nc + CHUNK - 1) / CHUNK);
-    }
-}
-
-// ===========================================================================
-// k_walk: every start walks next until a smaller half-edge (not a minimum)
-// or back to itself (a minimum: res = polygon length).  Grid-stride, one
-// chain per lane, two chains per thread interleaved, no block barrier.  The
-// 32 starts of a warp form one group, whose (minimum count, length) the warp
-// stores, and lie in one 2048-start chunk, whose total it adds with one
-// atomic.
-// ===========================================================================
-__global__ void __launch_bounds__(WALK_THREADS) k_walk(MeshView m, Work w) {
-    const int32_t HI = 3 * m.T;
-    const int32_t nc = w.ctrl->n_cand;
-    const int32_t G = gridDim.x * WALK_THREADS;
-    const int lane = threadIdx.x & 31;
-    // warp-uniform loop bounds: every lane of a warp runs the same rounds
-    const int32_t first = blockIdx.x * WALK_THREADS + (threadIdx.x & ~31);
-    for (int32_t b0 = first; b0 < nc; b0 += 2 * G) {
-        const int32_t i0 = b0 + lane;
-        const int32_t i1 = b0 + G + lane;
-        const bool h0 = i0 < nc, h1 = i1 < nc;
-        const int32_t e0 = h0 ? w.cand[i0] : 0;
-        const int32_t e1 = h1 ? w.cand[i1] : 0;
-        int32_t x0 = h0 ? m.next[e0] : -1;  // -1 < e: chain idle
-        int32_t x1 = h1 ? m.next[e1] : -1;
-        int32_t L0 = 1, L1 = 1, guard = 0;
-        while (x0 > e0 || x1 > e1) {
-            if (x0 > e0) { x0 = m.next[x0]; L0++; }
-            if (x1 > e1) { x1 = m.next[x1]; L1++; }
-            if (++guard > HI) {
-                atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
-                x0 = -1;
-                x1 = -1;
-                break;
-            }
-        }
-        const int32_t r0 = (h0 && x0 == e0) ? L0 : 0;
-        const int32_t r1 = (h1 && x1 == e1) ? L1 : 0;
-        if (h0) w.res[i0] = r0;
-        if (h1) w.res[i1] = r1;
-        const unsigned long long p0 = r0 > 0 ? ((1ull << 32) | (uint32_t)r0) : 0ull;
-        const unsigned long long p1 = r1 > 0 ? ((1ull << 32) | (uint32_t)r1) : 0ull;
-        const unsigned long long s0 = warp_sum(p0);
-        const unsigned long long s1 = warp_sum(p1);
+    const int64_t rec = (int64_t)tile * NT + threadIdx.x;
+    const unsigned long long ex = w.poly_rec[rec];
+    uint32_t minmask = w.poly_min[rec];
+    // the warps before this one in the tile, and this warp's own total
+    const unsigned long long wt = lane <= wid ? w.poly_wtot[(int64_t)tile * NW + lane] : 0ull;
+    const unsigned long long wbase = warp_sum(lane < wid ? wt : 0ull);
+    const unsigned long long wtot = __shfl_sync(0xffffffffu, wt, wid);
+    // the tiles before this one
+    const unsigned long long tbase = w.tile_pre[tile];
+    if (!__all_sync(0xffffffffu, mbar_wait(&s_bar, 0))) {
         if (lane == 0) {
-            if (b0 < nc) w.grp[b0 / 32] = s0;
-            if (b0 + G < nc) w.grp[(b0 + G) / 32] = s1;
-            if (s0 && b0 < nc) atomicAdd(&w.blk_b[b0 / CHUNK], s0);
-            if (s1 && b0 + G < nc) atomicAdd(&w.blk_b[(b0 + G) / CHUNK], s1);
+            atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
+            if (wid == 0) mbar_wait(&s_bar, 0);
         }
+        return;
     }
-}
-
-// ===========================================================================
-// k_emit: grid-stride over groups of 64 starts, one warp each (two starts
-// per lane).  A warp scan of the (count, length) pairs, plus the chunk's
-// scanned total and the 32-start group totals of the chunk before this
-// group, gives every minimum its polygon index and offset; no block
-// barrier, so a long polygon holds up its own warp only.  Each lane lists
-// its polygons from the minimum along next, interleaved, into the warp's
-// shared buffer (entries past it go out directly); the warp then stores
-// the buffer, one contiguous range of he_list and v_list, coalesced.
-// ===========================================================================
-__global__ void __launch_bounds__(EMIT_THREADS) k_emit(MeshView m, Work w) {
-    __shared__ int32_t s_he[EMIT_THREADS / 32][EMIT_BUF];
-    __shared__ int32_t s_v[EMIT_THREADS / 32][EMIT_BUF];
-    static_assert(CHUNK % 64 == 0, "groups of 64 starts do not straddle chunks");
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t HI = 3 * m.T;
-    const int32_t nc = w.ctrl->n_cand;
-    const int32_t n_sg = (nc + 63) / 64;
-    const int32_t nwarps = gridDim.x * (EMIT_THREADS / 32);
-    int32_t *bhe = s_he[wid];
-    int32_t *bv = s_v[wid];
-    for (int32_t sg = blockIdx.x * (EMIT_THREADS / 32) + wid; sg < n_sg; sg += nwarps) {
-        const int32_t c0 = sg * 64 + 2 * lane;
-        int32_t L0 = 0, L1 = 0;
-        if (c0 + 1 < nc) {
-            const int2 r = *reinterpret_cast<const int2 *>(w.res + c0);  // c0 is even: 8-byte aligned
-            L0 = r.x;
-            L1 = r.y;
-        } else if (c0 < nc) {
-            L0 = w.res[c0];
-        }
-        const unsigned long long q0 = L0 > 0 ? ((1ull << 32) | (uint32_t)L0) : 0ull;
-        const unsigned long long q1 = L1 > 0 ? ((1ull << 32) | (uint32_t)L1) : 0ull;
-        const unsigned long long inc = warp_incl_scan(q0 + q1, lane);
-        const unsigned long long ex = inc - (q0 + q1);
-        const unsigned long long tot = __shfl_sync(0xffffffffu, inc, 31);
-        // groups of 32 starts [g0, gs) precede this one in its chunk (< 64)
-        const int32_t ch = (sg * 64) / CHUNK;
-        const int32_t g0 = ch * (CHUNK / 32), gs = 2 * sg;
-        unsigned long long u = 0;
-        if (g0 + lane < gs) u += w.grp[g0 + lane];
-        if (g0 + 32 + lane < gs) u += w.grp[g0 + 32 + lane];
-        const unsigned long long base = w.blk_b_pre[ch] + warp_sum(u);
-        const int32_t O0 = (int32_t)(base & 0xffffffffu);
-        const int32_t len = (int32_t)(tot & 0xffffffffu);
-        if ((int64_t)(base >> 32) + (int64_t)(tot >> 32) > (int64_t)m.T || (int64_t)O0 + len > (int64_t)HI) {
-            if (lane == 0) atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
-            continue;  // warp-uniform
-        }
-        int32_t ea = -1, ka = 0, eb = -1, kb = 0;  // offsets within the group's range
-        if (L0 > 0) {
-            const unsigned long long r = base + ex;
-            ea = w.cand[c0];
-            ka = (int32_t)(ex & 0xffffffffu);
-            w.seeds[(int32_t)(r >> 32)] = ea;
-            w.offsets[(int32_t)(r >> 32)] = (int32_t)(r & 0xffffffffu);
-        }
-        if (L1 > 0) {
-            const unsigned long long r = base + ex + q0;
-            eb = w.cand[c0 + 1];
-            kb = (int32_t)((ex + q0) & 0xffffffffu);
-            w.seeds[(int32_t)(r >> 32)] = eb;
-            w.offsets[(int32_t)(r >> 32)] = (int32_t)(r & 0xffffffffu);
-        }
+    const unsigned long long base = tbase + wbase;  // this warp's first polygon and entry
+    const int64_t P0 = (int64_t)(base >> 32);
+    const int64_t NF0 = (int64_t)(base & 0xffffffffull);
+    const int64_t wlen = (int64_t)(wtot & 0xffffffffull);
+    if (P0 + (int64_t)(wtot >> 32) > (int64_t)m.T || NF0 + wlen > (int64_t)HI) {
+        if (lane == 0) atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+        return;  // warp-uniform
+    }
+    int32_t p = (int32_t)(P0 + (int64_t)(ex >> 32));
+    int32_t pos = (int32_t)(ex & 0xffffffffull);  // within the warp's range
+    int32_t *he_out = w.he_list + NF0;
+    int32_t *v_out = w.v_list + NF0;
+    int32_t *st_he = s_stage + wid * 2 * WCAP;
+    int32_t *st_v = st_he + WCAP;
+    const int32_t lt0 = (int32_t)threadIdx.x * IPT;
+    while (minmask) {
+        const int b = __ffs(minmask) - 1;
+        minmask &= minmask - 1u;
+        const int32_t e = eb + 3 * (lt0 + b / 3) + b % 3;
+        w.seeds[p] = e;
+        w.offsets[p] = (int32_t)NF0 + pos;
+        p++;
         // in a batch, lists are written in the mesh's own indices
-        int32_t she_a = 0, sv_a = 0, she_b = 0, sv_b = 0;
+        int32_t she = 0, sv = 0;
         if (w.loc_n > 0) {
-            if (ea >= 0) {
-                const int32_t i = seg_of(w.loc_t_off, w.loc_n, ea / 3);
-                she_a = 3 * __ldg(w.loc_t_off + i);
-                sv_a = __ldg(w.loc_v_off + i);
-            }
-            if (eb >= 0) {
-                const int32_t i = seg_of(w.loc_t_off, w.loc_n, eb / 3);
-                she_b = 3 * __ldg(w.loc_t_off + i);
-                sv_b = __ldg(w.loc_v_off + i);
-            }
+            const int32_t i = seg_of(w.loc_t_off, w.loc_n, e / 3);
+            she = 3 * __ldg(w.loc_t_off + i);
+            sv = __ldg(w.loc_v_off + i);
         }
-        int32_t xa = ea, xb = eb, guard = 0;
-        bool a = ea >= 0, b = eb >= 0;
-        while (a || b) {
-            if (a) {
-                const int32_t va = __ldg(m.origin + xa) - sv_a;
-                if (ka < EMIT_BUF) {
-                    bhe[ka] = xa - she_a;
-                    bv[ka] = va;
-                } else {
-                    w.he_list[O0 + ka] = xa - she_a;
-                    w.v_list[O0 + ka] = va;
-                }
-                ka++;
-                xa = m.next[xa];
-                a = xa != ea;
+        int32_t x = e;
+        int32_t guard = 0;
+        do {  // k_poly_count's walk came back to e: this loop ends
+            const uint32_t d = (uint32_t)(x - eb);
+            const bool in = d < ne;
+            const int32_t v = (in ? s_org[d] : __ldg(m.origin + x)) - sv;
+            if (pos < WCAP) {
+                st_he[pos] = x - she;
+                st_v[pos] = v;
+            } else {
+                he_out[pos] = x - she;
+                v_out[pos] = v;
             }
-            if (b) {
-                const int32_t vb = __ldg(m.origin + xb) - sv_b;
-                if (kb < EMIT_BUF) {
-                    bhe[kb] = xb - she_b;
-                    bv[kb] = vb;
-                } else {
-                    w.he_list[O0 + kb] = xb - she_b;
-                    w.v_list[O0 + kb] = vb;
-                }
-                kb++;
-                xb = m.next[xb];
-                b = xb != eb;
-            }
-            if (++guard > HI) break;
-        }
-        __syncwarp();
-        const int32_t nb = min(len, EMIT_BUF);
-        for (int32_t k = lane; k < nb; k += 32) {
-            w.he_list[O0 + k] = bhe[k];
-            w.v_list[O0 + k] = bv[k];
-        }
-        __syncwarp();  // the buffer is reused by the warp's next group
+            pos++;
+            x = in ? s_nx[d] : __ldg(m.next + x);
+        } while (x != e && ++guard < HI);
+    }
+    __syncwarp();
+    const int32_t nb = (int32_t)min(wlen, (int64_t)WCAP);
+    for (int32_t k = lane; k < nb; k += 32) {
+        he_out[k] = st_he[k];
+        v_out[k] = st_v[k];
     }
 }
 
-void launch_scan_u64(const unsigned long long *in, unsigned long long *out, int32_t n, unsigned long long *grand,
-                     cudaStream_t s) {
-    k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, 0, grand, MeshView{}, Work{}, 0);
+// ---- launch configurations (tile triangles, threads per CTA) ---------------
+template <int TILE>
+constexpr size_t count_smem() {
+    return (size_t)3 * TILE * sizeof(int32_t) + TILE;
+}
+template <int TILE>
+constexpr size_t list_smem() {
+    // next and origin of the tile, and per warp 2 x 64 x (TILE / NT) staged
+    // entries: 4 TILE ints in all
+    return (size_t)(2 * 3 * TILE + 4 * TILE) * sizeof(int32_t);
 }
 
-int polygons_configure() { return 0; }
+#define POLYGON_CONFIGS(X) \
+    X(1024, 256)           \
+    X(1024, 128)           \
+    X(2048, 512)           \
+    X(2048, 256)           \
+    X(4096, 1024)          \
+    X(4096, 512)
 
-int emit_blocks_per_sm() {
+bool polygons_config_valid(int32_t tile, int32_t items) {
+#define X(TL, N) \
+    if (tile == TL && items == TL / N) return true;
+    POLYGON_CONFIGS(X)
+#undef X
+    return false;
+}
+
+int polygons_configure() {
+#define X(TL, N)                                                                                             \
+    if (cudaFuncSetAttribute(k_poly_count<TL, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                             (int)count_smem<TL>()) != cudaSuccess ||                                        \
+        cudaFuncSetAttribute(k_poly_list<TL, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+                             (int)list_smem<TL>()) != cudaSuccess)                                           \
+        return -1;
+    POLYGON_CONFIGS(X)
+#undef X
+    return 0;
+}
+
+// resident CTAs per SM of the listing kernel (the larger of the two)
+int polygons_blocks_per_sm(int32_t tile, int32_t items) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_emit, EMIT_THREADS, 0) != cudaSuccess || nb < 1) nb = 1;
+#define X(TL, N)                                                                                          \
+    if (tile == TL && items == TL / N) {                                                                  \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_poly_list<TL, N>, N, list_smem<TL>()) != \
+            cudaSuccess)                                                                                  \
+            nb = 0;                                                                                       \
+    }
+    POLYGON_CONFIGS(X)
+#undef X
     return nb;
 }
 
-void launch_cand_count(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_cand_count<<<w.n_cc_blocks, CC_THREADS, 0, s>>>(m, w);
+// the two kernels of the output stage (an unknown configuration takes the
+// default one: the tuning entry points accept only valid ones)
+void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s) {
+#define X(TL, N)                                                                            \
+    if (w.out_tile == TL && w.out_items == TL / N) {                                        \
+        k_poly_count<TL, N><<<(m.T + TL - 1) / TL, N, count_smem<TL>(), s>>>(m, w);         \
+        return;                                                                             \
+    }
+    POLYGON_CONFIGS(X)
+#undef X
+    k_poly_count<2048, 512><<<(m.T + 2047) / 2048, 512, count_smem<2048>(), s>>>(m, w);
 }
 
-void launch_cand_scan(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(w.blk_a, w.blk_a_pre, w.n_cc_blocks, nullptr, 0,
-                                             &w.ctrl->n_cand64, m, w, 0);
+void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s) {
+    const int32_t tile = polygons_config_valid(w.out_tile, w.out_items) ? w.out_tile : 2048;
+    k_tile_scan<<<1, SCAN_THREADS, 0, s>>>(m, w, (m.T + tile - 1) / tile);
 }
 
-void launch_cand_write(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_cand_write<<<w.n_cc_blocks, CC_THREADS, 0, s>>>(m, w);
-}
-
-void launch_walk(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_walk<<<w.walk_blocks, WALK_THREADS, 0, s>>>(m, w);
-}
-
-void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(w.blk_b, w.blk_b_pre, -1, &w.ctrl->n_chunks, w.n_chunk_max,
-                                             &w.ctrl->grand_b, m, w, 1);
-}
-
-void launch_emit(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_emit<<<w.emit_blocks, EMIT_THREADS, 0, s>>>(m, w);
+void launch_poly_list(const MeshView &m, const Work &w, cudaStream_t s) {
+#define X(TL, N)                                                                            \
+    if (w.out_tile == TL && w.out_items == TL / N) {                                        \
+        k_poly_list<TL, N><<<(m.T + TL - 1) / TL, N, list_smem<TL>(), s>>>(m, w);           \
+        return;                                                                             \
+    }
+    POLYGON_CONFIGS(X)
+#undef X
+    k_poly_list<2048, 512><<<(m.T + 2047) / 2048, 512, list_smem<2048>(), s>>>(m, w);
 }
 
 }  // namespace polylla

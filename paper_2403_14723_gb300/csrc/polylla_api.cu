@@ -14,13 +14,14 @@ using namespace polylla;
 
 namespace {
 
-constexpr int kCore = 10;    // the method's stages, on one mesh or a batch's union
-constexpr int kStages = 12;  // + batch packing and unpacking
+constexpr int kCore = 7;     // the method's kernels, on one mesh or a batch's union
+constexpr int kStages = 9;   // + batch packing and unpacking
+constexpr int kPack = 7, kUnpack = 8;
 const char *kStageNames[kStages] = {
-    "longest_edge", "label_relink", "chords", "chord_links", "cand_count",
-    "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack",
+    "longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan", "poly_list",
+    "batch_pack", "batch_unpack",
 };
-constexpr int kKernels = 10;       // one kernel per stage
+constexpr int kKernels = 7;        // one kernel per stage
 constexpr int kBatchKernels = 5;   // pack (interior, border); unpack; ranges (two kernels)
 
 }  // namespace
@@ -157,24 +158,24 @@ static int sm_count(polylla_ctx *c) {
 
 static bool tuning_valid(polylla_ctx *c, const polylla_tuning &t) {
     const int cap = 64 * sm_count(c);
-    auto in = [&](int32_t v) { return v >= 1 && v <= cap; };
     return (t.relink_threads == 64 || t.relink_threads == 128 || t.relink_threads == 256) &&
-           in(t.longest_edge_blocks) && in(t.walk_blocks) && in(t.emit_blocks);
+           t.longest_edge_blocks >= 1 && t.longest_edge_blocks <= cap &&
+           polygons_config_valid(t.output_tile, t.output_items);
 }
 
 static void apply_tuning(polylla_ctx *c, const polylla_tuning &t) {
     c->w.rl_threads = t.relink_threads;
     c->w.le_blocks = t.longest_edge_blocks;
-    c->w.walk_blocks = t.walk_blocks;
-    c->w.emit_blocks = t.emit_blocks;
+    c->w.out_tile = t.output_tile;
+    c->w.out_items = t.output_items;
 }
 
 static polylla_tuning current_tuning(const polylla_ctx *c) {
     polylla_tuning t;
     t.relink_threads = c->w.rl_threads;
     t.longest_edge_blocks = c->w.le_blocks;
-    t.walk_blocks = c->w.walk_blocks;
-    t.emit_blocks = c->w.emit_blocks;
+    t.output_tile = c->w.out_tile;
+    t.output_items = c->w.out_items;
     return t;
 }
 
@@ -201,22 +202,17 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.tips = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)V))) return rc;
     c->w.chords = (int32_t *)p;
-    c->w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
-    c->w.n_chunk_max = (int32_t)((HI + CHUNK - 1) / CHUNK);
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_cc_blocks))) return rc;
-    c->w.blk_a = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_cc_blocks))) return rc;
-    c->w.blk_a_pre = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_chunk_max))) return rc;
-    c->w.blk_b = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_chunk_max))) return rc;
-    c->w.blk_b_pre = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)((HI + 31) / 32)))) return rc;
-    c->w.grp = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)HI))) return rc;
-    c->w.cand = (int32_t *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)HI))) return rc;
-    c->w.res = (int32_t *)p;
+    c->w.n_tile_max = (int32_t)(((int64_t)T + OUT_TILE_MIN - 1) / OUT_TILE_MIN);
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tile_max))) return rc;
+    c->w.tile_state = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tile_max))) return rc;
+    c->w.tile_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)out_rec_count(T)))) return rc;
+    c->w.poly_rec = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(uint32_t) * (size_t)out_rec_count(T)))) return rc;
+    c->w.poly_min = (uint32_t *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)out_warp_count(T)))) return rc;
+    c->w.poly_wtot = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)T))) return rc;
     c->w.seeds = (int32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)(T + 1)))) return rc;
@@ -244,8 +240,8 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
     c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
-    c->w.walk_blocks = 8 * (sms > 0 ? sms : 1);
-    c->w.emit_blocks = emit_blocks_per_sm() * (sms > 0 ? sms : 1);
+    c->w.out_tile = OUT_TILE_DEFAULT;
+    c->w.out_items = OUT_ITEMS_DEFAULT;
     c->w.rl_threads = RL_THREADS;
     if (polygons_configure() != 0) return cuda_fail(c, cudaGetLastError());
     c->w.max_rot = (opt && opt->max_rotation > 0) ? opt->max_rotation : 4096;
@@ -318,7 +314,7 @@ const char *polylla_status_string(int status) {
         case POLYLLA_ERR_NONTERMINATING: return "rotation or cycle walk did not terminate";
         case POLYLLA_ERR_CAPACITY: return "internal list capacity exceeded";
         case POLYLLA_ERR_TIMEOUT: return "device wait timed out";
-        case POLYLLA_ERR_TOO_LARGE: return "mesh larger than the no-allocation scratch";
+        case POLYLLA_ERR_TOO_LARGE: return "mesh larger than the available capacity (no-allocation scratch or server slot)";
         default: return "unknown status";
     }
 }
@@ -407,15 +403,14 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
     };
     auto end = [&](int i) -> cudaError_t { return timing ? cudaEventRecord(c->ev_end[i], s) : cudaSuccess; };
     if (c->is_batch) {
-        CK(begin(10));
+        CK(begin(kPack));
         CK(cudaMemsetAsync(c->w.input_err, 0, sizeof(int32_t), s));
         launch_batch_pack(c->bv, c->u_origin, c->u_twin, nullptr, nullptr, nullptr, c->w.input_err, s);
-        CK(end(10));
+        CK(end(kPack));
     }
     void (*stages[kCore])(const MeshView &, const Work &, cudaStream_t) = {
-        launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links,
-        launch_cand_count, launch_cand_scan, launch_cand_write, launch_walk,
-        launch_chunk_scan, launch_emit,
+        launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links, launch_poly_count,
+        launch_tile_scan, launch_poly_list,
     };
     for (int i = 0; i < kCore; i++) {
         if (i == 1 && c->wait_before_relink) CK(cudaStreamWaitEvent(s, c->wait_before_relink, 0));
@@ -425,11 +420,11 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
         if (i == 3 && c->record_after_links) CK(cudaEventRecord(c->record_after_links, s));
     }
     if (c->is_batch) {
-        CK(begin(11));
+        CK(begin(kUnpack));
         launch_batch_unpack(c->bv, c->mesh, s);
         launch_batch_ranges(c->bv, c->w, c->poly_off, s);
         if (c->serve) launch_batch_meta(c->bv, c->w, c->poly_off, c->local_offsets, c->meta, s);
-        CK(end(11));
+        CK(end(kUnpack));
     }
     c->launches = kKernels + (c->is_batch ? kBatchKernels : 0) + (c->serve ? 1 : 0);
     CK(cudaGetLastError());
@@ -602,7 +597,7 @@ int polylla_get_stage_times(polylla_ctx *c, float *ms, int32_t n) {
     for (int i = 0; i < kStages; i++)
         if (c->stage_ran[i]) last = i;
     if (last < 0) return 0;
-    CK(cudaEventSynchronize(c->ev_end[c->is_batch ? 11 : kCore - 1]));
+    CK(cudaEventSynchronize(c->ev_end[c->is_batch ? kUnpack : kCore - 1]));
     const int k = n < kStages ? n : kStages;
     for (int i = 0; i < k; i++) {
         float t = 0.f;
@@ -728,8 +723,8 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
     const bool timing = c->timing;
     c->timing = true;
     const int sms = sm_count(c);
-    // median time of one stage over reps whole runs
-    auto stage_ms = [&](int stage, float *med) -> int {
+    // median time of stages [stage, last] over reps whole runs
+    auto stage_ms = [&](int stage, int last, float *med) -> int {
         float v[64];
         const int r = reps < 64 ? reps : 64;
         for (int i = 0; i < r; i++) {
@@ -737,7 +732,8 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
             if (rc) return rc;
             float ms[kStages];
             if (polylla_get_stage_times(c, ms, kStages) != kStages) return POLYLLA_ERR_CUDA;
-            v[i] = ms[stage];
+            v[i] = 0.f;
+            for (int k = stage; k <= last; k++) v[i] += ms[k];
         }
         for (int i = 1; i < r; i++)  // insertion sort, r is small
             for (int j = i; j > 0 && v[j] < v[j - 1]; j--) {
@@ -748,41 +744,51 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
         *med = v[r / 2];
         return POLYLLA_OK;
     };
-    struct Knob {
-        int stage;
-        int32_t *field;
-        int32_t cand[8];
-        int n;
-    };
-    const int le_occ = longest_edge_blocks_per_sm(), em_occ = emit_blocks_per_sm();
-    Knob knobs[4] = {
-        {1, &c->w.rl_threads, {64, 128, 256}, 3},
-        {0, &c->w.le_blocks, {0}, 0},
-        {7, &c->w.walk_blocks, {2 * sms, 4 * sms, 8 * sms, 16 * sms}, 4},
-        {9, &c->w.emit_blocks, {0}, 0},
-    };
-    for (int k = 1; k <= le_occ && knobs[1].n < 8; k++) knobs[1].cand[knobs[1].n++] = k * sms;
-    for (int k = 1; k <= em_occ && knobs[3].n < 8; k++) knobs[3].cand[knobs[3].n++] = k * sms;
+    // one knob per stage, tried in stage order: its candidates are whole
+    // tunings that differ from the current one in that knob's fields only
+    const int le_occ = longest_edge_blocks_per_sm();
     int rc = POLYLLA_OK;
-    for (int q = 0; q < 4 && !rc; q++) {
-        Knob &kb = knobs[q];
-        int32_t best = *kb.field;
+    for (int q = 0; q < 3 && !rc; q++) {
+        // relink, longest edge, the output kernels (count, scan, list)
+        const int stage = q == 0 ? 1 : (q == 1 ? 0 : 4), last = q == 2 ? 6 : stage;
+        polylla_tuning cand[16];
+        int n = 0;
+        const polylla_tuning cur = current_tuning(c);
+        if (q == 0) {
+            for (int32_t v : {64, 128, 256}) {
+                cand[n] = cur;
+                cand[n++].relink_threads = v;
+            }
+        } else if (q == 1) {
+            for (int k = 1; k <= le_occ && n < 8; k++) {
+                cand[n] = cur;
+                cand[n++].longest_edge_blocks = k * sms;
+            }
+        } else {
+            // output tile and triangles per thread (the launch configurations
+            // the library is built with)
+            const int32_t pairs[][2] = {{1024, 4}, {1024, 8}, {2048, 4}, {2048, 8}, {4096, 4}, {4096, 8}};
+            for (const auto &pr : pairs)
+                if (polygons_config_valid(pr[0], pr[1]) && polygons_blocks_per_sm(pr[0], pr[1]) > 0) {
+                    cand[n] = cur;
+                    cand[n].output_tile = pr[0];
+                    cand[n++].output_items = pr[1];
+                }
+        }
+        polylla_tuning best = cur;
         float best_ms = 0.f;
-        rc = stage_ms(kb.stage, &best_ms);
-        for (int i = 0; i < kb.n && !rc; i++) {
-            if (kb.cand[i] == best) continue;
-            const int32_t keep = *kb.field;
-            *kb.field = kb.cand[i];
+        rc = stage_ms(stage, last, &best_ms);
+        for (int i = 0; i < n && !rc; i++) {
+            if (memcmp(&cand[i], &best, sizeof(best)) == 0) continue;
+            apply_tuning(c, cand[i]);
             float t = 0.f;
-            rc = stage_ms(kb.stage, &t);
+            rc = stage_ms(stage, last, &t);
             if (!rc && t < best_ms) {
                 best_ms = t;
-                best = kb.cand[i];
-            } else {
-                *kb.field = keep;
+                best = cand[i];
             }
         }
-        *kb.field = best;
+        apply_tuning(c, best);
     }
     c->timing = timing;
     if (rc) return rc;
@@ -875,8 +881,7 @@ int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const 
     c->bv.T_tot = T;
     c->bv.H_tot = H;
     c->w.loc_n = n;
-    c->w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
-    c->w.n_chunk_max = (int32_t)((3 * (int64_t)T + CHUNK - 1) / CHUNK);
+    c->w.n_tile_max = (int32_t)(((int64_t)T + OUT_TILE_MIN - 1) / OUT_TILE_MIN);
     launch_serve_offsets(off4, n, const_cast<int32_t *>(c->bv.v_off), const_cast<int32_t *>(c->bv.t_off),
                          const_cast<int32_t *>(c->bv.h_off), const_cast<int32_t *>(c->bv.b_off), s);
     c->last_stream = s;

@@ -8,11 +8,11 @@
 //                        bit 6 the triangle's longest half-edge is a seed
 //   tips    [V]   int32  F0 half-edge leaving each barrier tip
 //   chords  [V]   int32  chord half-edge leaving each barrier tip
-//   cand  [3T]    int32  walk starts (marked frontier half-edges), ascending
-//   res   [3T]    int32  polygon length of each start that is a minimum, else 0
-//   blk_a/blk_a_pre   u64  start counts per CC_TRI triangles, scanned
-//   blk_b/blk_b_pre   u64  (polygons, length) per CHUNK starts, scanned
-//   grp   [3T/32] u64    (polygons, length) per 32 starts
+//   tile_state, tile_pre [T/1024] u64  (polygons, length) total of each output
+//                        tile, and their exclusive scan
+//   poly_rec [T/4+1025] u64, poly_min [..] u32   per output thread: its
+//                        (polygons, length) offset in its warp's range, its minima
+//   poly_wtot [T/128+34] u64  per output warp: its (polygons, length) total
 //   seeds [T], offsets [T+1], he_list [3T], v_list [3T]   CSR output
 //   ctrl          DevCtrl       counters and the device error word
 // A batch context adds the union origin/twin/next/prev [H], the per-mesh
@@ -33,15 +33,11 @@ enum : int32_t {
 };
 
 struct DevCtrl {
-    int32_t error;       // OR of DEV_ERR_* bits of this generate
-    int32_t n_tips;      // barrier tips found by the relink
-    int32_t n_polygons;  // P
-    int32_t n_frontier;  // N_F
-    int32_t n_cand;      // walk starts
-    int32_t n_chunks;    // 2048-start chunks
-    int32_t pad[2];
-    unsigned long long n_cand64;  // walk starts, as scanned
-    unsigned long long grand_b;   // (P << 32 | N_F), as scanned
+    int32_t error;        // OR of DEV_ERR_* bits of this generate
+    int32_t n_tips;       // barrier tips found by the relink
+    int32_t n_polygons;   // P
+    int32_t n_frontier;   // N_F
+    int32_t pad[4];
 };
 
 struct MeshView {
@@ -59,16 +55,14 @@ struct Work {
     int32_t *tips;
     int32_t *chords;
     int32_t tip_cap;
-    unsigned long long *blk_a;      // walk starts per block of CC_TRI triangles
-    unsigned long long *blk_a_pre;  // their exclusive prefix
-    int32_t *cand;                  // walk starts in index order [3T]
-    int32_t *res;                   // polygon length per start, 0 if not a minimum [3T]
-    unsigned long long *blk_b;      // (minimum count, length) per CHUNK starts
-    unsigned long long *blk_b_pre;  // their exclusive prefix
-    unsigned long long *grp;        // (minimum count, length) per 32 starts [ceil(3T/32)]
-    int32_t n_cc_blocks;            // ceil(T / CC_TRI)
-    int32_t n_chunk_max;            // ceil(3T / CHUNK)
-    int32_t walk_blocks, emit_blocks;
+    unsigned long long *tile_state; // (polygons, length) total per output tile [n_tile_max]
+    unsigned long long *tile_pre;   // their exclusive scan [n_tile_max]
+    unsigned long long *poly_rec;   // per output thread: place in its tile [n_rec_max]
+    uint32_t *poly_min;             // per output thread: mask of its minima [n_rec_max]
+    unsigned long long *poly_wtot;  // per output warp: (polygons, length) of its range
+    int32_t n_tile_max;             // ceil(T / OUT_TILE_MIN)
+    int32_t out_tile;               // output tile: triangles
+    int32_t out_items;              // output kernel: triangles per thread
     int32_t rl_threads;             // relink block size: 64, 128 or 256
     int32_t *seeds;
     int32_t *offsets;
@@ -103,19 +97,17 @@ struct BatchView {
     int32_t *prev;
 };
 
-// output kernels: start counting/compaction over blocks of CC_TRI
-// triangles (16 per thread, one int4 of flags), walks and emission per warp
-// over groups of 32 and 64 starts inside chunks of CHUNK starts,
-// single-block scans of the block and chunk totals
-constexpr int CC_THREADS = 1024;
-constexpr int CC_PER = 16;
-constexpr int CC_TRI = CC_THREADS * CC_PER;
-constexpr int CW_BUF = 10240;  // walk starts a block stages in shared memory (40 KB)
+// output kernel: tiles of out_tile triangles (1024, 2048 or 4096), out_items
+// per thread; single-block scans (Lepp paths) with SCAN_THREADS threads
+constexpr int OUT_TILE_MIN = 1024;
+constexpr int OUT_TILE_MAX = 4096;
+constexpr int OUT_ITEMS_MIN = 4;
+constexpr int OUT_TILE_DEFAULT = 2048;
+constexpr int OUT_ITEMS_DEFAULT = 4;
+// per-thread records of the output stage for T triangles, any configuration
+__host__ __device__ constexpr int64_t out_rec_count(int64_t T) { return (T + OUT_TILE_MAX) / OUT_ITEMS_MIN + 1; }
+__host__ __device__ constexpr int64_t out_warp_count(int64_t T) { return out_rec_count(T) / 32 + 2; }
 constexpr int SCAN_THREADS = 1024;
-constexpr int CHUNK = 2048;
-constexpr int WALK_THREADS = 256;
-constexpr int EMIT_THREADS = 512;
-constexpr int EMIT_BUF = 256;  // CSR entries staged per warp
 
 // longest-edge kernel: persistent warps, each with a two-stage ring of
 // 64-triangle tiles of origin bulk-copied (TMA) into shared memory
@@ -204,14 +196,14 @@ int longest_edge_blocks_per_sm();
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chords(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_cand_count(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_cand_scan(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_cand_write(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_walk(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_chunk_scan(const MeshView &m, const Work &w, cudaStream_t s);
-void launch_emit(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_poly_list(const MeshView &m, const Work &w, cudaStream_t s);
+// allows the output kernels their shared memory on the current device (once
+// per device before the first launch); 0 on success
 int polygons_configure();
-int emit_blocks_per_sm();
+bool polygons_config_valid(int32_t tile, int32_t items);
+int polygons_blocks_per_sm(int32_t tile, int32_t items);
 // exclusive scan of n u64 values by one block; *grand gets the sum
 void launch_scan_u64(const unsigned long long *in, unsigned long long *out, int32_t n, unsigned long long *grand,
                      cudaStream_t s);

@@ -2,13 +2,13 @@
 //
 // Some callers of this library cannot call cudaMalloc: a serving loop that
 // must not allocate once it is running (an allocation can stall on the
-// device, fail under a full memory budget, or fragment a pool that a
-// caching allocator manages), code recorded into a CUDA graph, or a host
-// whose device memory is entirely owned by another allocator.  This entry
-// point runs the same kernels as polylla_generate, with every scratch
-// buffer carved from one file-scope __device__ array of fixed size; the
-// caller passes the mesh and the output buffers.  It allocates nothing and
-// frees nothing, on the device or on the host.
+// device or fail under a full memory budget), or a process whose device
+// memory is entirely owned by another allocator, which a stray cudaMalloc
+// would bypass or fragment.  This entry point runs the same kernels as
+// polylla_generate, with every scratch buffer carved from one file-scope
+// __device__ array of fixed size; the caller passes the mesh and the output
+// buffers.  It allocates nothing and frees nothing, on the device or on the
+// host.
 #include <cstring>
 #include <mutex>
 
@@ -22,9 +22,7 @@ namespace {
 constexpr int32_t NA_MAX_T = POLYLLA_NOALLOC_MAX_TRIANGLES;
 // a triangulated disk has V = (T + B + 2) / 2 with B <= T + 2 boundary edges
 constexpr int32_t NA_MAX_V = NA_MAX_T + 2;
-constexpr int64_t NA_MAX_HI = 3 * (int64_t)NA_MAX_T;
-constexpr int64_t NA_MAX_CC = ((int64_t)NA_MAX_T + CC_TRI - 1) / CC_TRI;
-constexpr int64_t NA_MAX_CHUNKS = (NA_MAX_HI + CHUNK - 1) / CHUNK;
+constexpr int64_t NA_MAX_TILES = ((int64_t)NA_MAX_T + OUT_TILE_MIN - 1) / OUT_TILE_MIN;
 
 constexpr size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 // layout of the scratch array (byte offsets, each 256-aligned)
@@ -32,14 +30,12 @@ constexpr size_t OFF_LE = 0;
 constexpr size_t OFF_FLAGS = OFF_LE + up256(NA_MAX_T);
 constexpr size_t OFF_TIPS = OFF_FLAGS + up256(NA_MAX_T);
 constexpr size_t OFF_CHORDS = OFF_TIPS + up256(4 * (size_t)NA_MAX_V);
-constexpr size_t OFF_BLK_A = OFF_CHORDS + up256(4 * (size_t)NA_MAX_V);
-constexpr size_t OFF_BLK_A_PRE = OFF_BLK_A + up256(8 * (size_t)NA_MAX_CC);
-constexpr size_t OFF_BLK_B = OFF_BLK_A_PRE + up256(8 * (size_t)NA_MAX_CC);
-constexpr size_t OFF_BLK_B_PRE = OFF_BLK_B + up256(8 * (size_t)NA_MAX_CHUNKS);
-constexpr size_t OFF_GRP = OFF_BLK_B_PRE + up256(8 * (size_t)NA_MAX_CHUNKS);
-constexpr size_t OFF_CAND = OFF_GRP + up256(8 * (size_t)((NA_MAX_HI + 31) / 32));
-constexpr size_t OFF_RES = OFF_CAND + up256(4 * (size_t)NA_MAX_HI);
-constexpr size_t OFF_CTRL = OFF_RES + up256(4 * (size_t)NA_MAX_HI);
+constexpr size_t OFF_TILES = OFF_CHORDS + up256(4 * (size_t)NA_MAX_V);
+constexpr size_t OFF_TILE_PRE = OFF_TILES + up256(8 * (size_t)NA_MAX_TILES);
+constexpr size_t OFF_REC = OFF_TILE_PRE + up256(8 * (size_t)NA_MAX_TILES);
+constexpr size_t OFF_MIN = OFF_REC + up256(8 * (size_t)out_rec_count(NA_MAX_T));
+constexpr size_t OFF_WTOT = OFF_MIN + up256(4 * (size_t)out_rec_count(NA_MAX_T));
+constexpr size_t OFF_CTRL = OFF_WTOT + up256(8 * (size_t)out_warp_count(NA_MAX_T));
 constexpr size_t NA_BYTES = OFF_CTRL + up256(sizeof(DevCtrl));
 
 constexpr int kMaxDevices = 64;
@@ -47,26 +43,33 @@ constexpr int kMaxDevices = 64;
 }  // namespace
 
 // The scratch.  Every GPU that loads the library holds it (NA_BYTES, about
-// 4.5 MB) until the process exits.  In host code its name is only a host-side
+// 1.7 MB) until the process exits.  In host code its name is only a host-side
 // stand-in: the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 static std::mutex g_setup_lock;
 static unsigned char *g_scratch_addr[kMaxDevices];  // device address per device, set once
+static int g_sms[kMaxDevices];
 
-// Look up the scratch address on the current device (first call per device).
-static int scratch_address(unsigned char **out, int *device) {
+// Set-up, once per device, on the current device (the first call there):
+// look up the scratch array's device address, allow the output kernel its
+// shared memory, read the SM count.
+static int device_setup(unsigned char **out, int *sms) {
     int d = 0;
     if (cudaGetDevice(&d) != cudaSuccess) return POLYLLA_ERR_CUDA;
     if (d < 0 || d >= kMaxDevices) return POLYLLA_ERR_INVALID_ARGUMENT;
     std::lock_guard<std::mutex> guard(g_setup_lock);
     if (!g_scratch_addr[d]) {
         void *p = nullptr;
+        int n = 0;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return POLYLLA_ERR_CUDA;
+        if (polygons_configure() != 0) return POLYLLA_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) return POLYLLA_ERR_CUDA;
+        g_sms[d] = n > 0 ? n : 1;
         g_scratch_addr[d] = static_cast<unsigned char *>(p);
     }
     *out = g_scratch_addr[d];
-    *device = d;
+    *sms = g_sms[d];
     return POLYLLA_OK;
 }
 
@@ -83,13 +86,13 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     if (!aligned16(mesh->coords) || !aligned16(mesh->origin) || !aligned16(mesh->twin) ||
         !aligned16(mesh->next) || !aligned16(mesh->prev))
         return POLYLLA_ERR_INVALID_ARGUMENT;
+    // an error the caller left pending would be taken for one of ours by
+    // the launch check below: report it, leave it pending, launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return POLYLLA_ERR_CUDA;
     unsigned char *base = nullptr;
-    int device = 0;
-    int rc = scratch_address(&base, &device);
+    int sms = 1;
+    int rc = device_setup(&base, &sms);
     if (rc) return rc;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return POLYLLA_ERR_CUDA;
-    if (polygons_configure() != 0) return POLYLLA_ERR_CUDA;
 
     MeshView m{};
     m.V = V;
@@ -106,41 +109,36 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.tips = reinterpret_cast<int32_t *>(base + OFF_TIPS);
     w.chords = reinterpret_cast<int32_t *>(base + OFF_CHORDS);
     w.tip_cap = V;
-    w.blk_a = reinterpret_cast<unsigned long long *>(base + OFF_BLK_A);
-    w.blk_a_pre = reinterpret_cast<unsigned long long *>(base + OFF_BLK_A_PRE);
-    w.blk_b = reinterpret_cast<unsigned long long *>(base + OFF_BLK_B);
-    w.blk_b_pre = reinterpret_cast<unsigned long long *>(base + OFF_BLK_B_PRE);
-    w.grp = reinterpret_cast<unsigned long long *>(base + OFF_GRP);
-    w.cand = reinterpret_cast<int32_t *>(base + OFF_CAND);
-    w.res = reinterpret_cast<int32_t *>(base + OFF_RES);
-    w.n_cc_blocks = (int32_t)(((int64_t)T + CC_TRI - 1) / CC_TRI);
-    w.n_chunk_max = (int32_t)((3 * (int64_t)T + CHUNK - 1) / CHUNK);
+    w.tile_state = reinterpret_cast<unsigned long long *>(base + OFF_TILES);
+    w.tile_pre = reinterpret_cast<unsigned long long *>(base + OFF_TILE_PRE);
+    w.poly_rec = reinterpret_cast<unsigned long long *>(base + OFF_REC);
+    w.poly_min = reinterpret_cast<uint32_t *>(base + OFF_MIN);
+    w.poly_wtot = reinterpret_cast<unsigned long long *>(base + OFF_WTOT);
+    w.n_tile_max = (int32_t)(((int64_t)T + OUT_TILE_MIN - 1) / OUT_TILE_MIN);
     w.seeds = seeds;
     w.offsets = offsets;
     w.he_list = he_list;
     w.v_list = v_list;
     w.ctrl = reinterpret_cast<DevCtrl *>(base + OFF_CTRL);
     w.max_rot = 4096;
-    w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
-    w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
-    w.walk_blocks = 8 * (sms > 0 ? sms : 1);
-    w.emit_blocks = emit_blocks_per_sm() * (sms > 0 ? sms : 1);
+    w.persistent_blocks = 4 * sms;
+    w.le_blocks = longest_edge_blocks_per_sm() * sms;
+    w.out_tile = OUT_TILE_DEFAULT;
+    w.out_items = OUT_ITEMS_DEFAULT;
     w.rl_threads = RL_THREADS;
 
-    // The first kernel zeroes the control block and k_cand_count zeroes the
-    // chunk totals; every other scratch word is written before it is read,
-    // so the previous call's contents never leak into this one.
+    // The first kernel zeroes the control block (counters) and the output
+    // tiles' totals; every other scratch word is written
+    // before it is read, so the previous call's contents never leak into
+    // this one.
     cudaStream_t s = (cudaStream_t)stream;
     launch_longest_edge(m, w, s);
     launch_label_relink(m, w, s);
     launch_chords(m, w, s);
     launch_chord_links(m, w, s);
-    launch_cand_count(m, w, s);
-    launch_cand_scan(m, w, s);
-    launch_cand_write(m, w, s);
-    launch_walk(m, w, s);
-    launch_chunk_scan(m, w, s);
-    launch_emit(m, w, s);
+    launch_poly_count(m, w, s);
+    launch_tile_scan(m, w, s);
+    launch_poly_list(m, w, s);
     // status3 = {P, N_F, device error bits}, copied device to device
     if (cudaMemcpyAsync(status3, &w.ctrl->n_polygons, 2 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s) !=
             cudaSuccess ||

@@ -78,7 +78,7 @@ class polylla_batch(ctypes.Structure):
 
 class polylla_tuning(ctypes.Structure):
     _fields_ = [("relink_threads", ctypes.c_int32), ("longest_edge_blocks", ctypes.c_int32),
-                ("walk_blocks", ctypes.c_int32), ("emit_blocks", ctypes.c_int32)]
+                ("output_tile", ctypes.c_int32), ("output_items", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

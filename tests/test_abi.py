@@ -49,10 +49,10 @@ def test_status_strings_without_gpu(lib_path):
     lib = polylla.load_library()
     assert lib.polylla_status_string(0) == b"ok"
     assert lib.polylla_status_string(-2) == b"invalid mesh layout"
-    assert lib.polylla_stage_count() == 12
-    names = [lib.polylla_stage_name(i).decode() for i in range(12)]
-    assert names == ["longest_edge", "label_relink", "chords", "chord_links", "cand_count",
-                     "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack"]
+    assert lib.polylla_stage_count() == 9
+    names = [lib.polylla_stage_name(i).decode() for i in range(9)]
+    assert names == ["longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan",
+                     "poly_list", "batch_pack", "batch_unpack"]
 
 
 def test_null_arguments_rejected_without_gpu(lib_path):

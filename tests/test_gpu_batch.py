@@ -94,7 +94,7 @@ def assert_batch_parity(meshes, db, g):
 def test_batch_matches_oracle_per_mesh():
     meshes = _mix()
     db, g = batch_run(meshes)
-    assert g["launches"] == 15
+    assert g["launches"] == 12
     assert_batch_parity(meshes, db, g)
 
 
@@ -137,7 +137,11 @@ def test_single_mesh_graph_and_tuning_keep_results():
         with polylla.Polylla(dm, stream=stream) as p:
             t = polylla.polylla_autotune(p.ctx, reps=2, stream=stream)
             assert t["relink_threads"] in (64, 128, 256)
+            assert (t["output_tile"], t["output_items"]) in ((1024, 4), (1024, 8), (2048, 4), (2048, 8),
+                                                             (4096, 4), (4096, 8))
             assert polylla.polylla_get_tuning(p.ctx) == t
+            with pytest.raises(polylla.PolyllaError):
+                polylla.polylla_set_tuning(p.ctx, dict(t, output_tile=3072))
             with pytest.raises(polylla.PolyllaError):
                 polylla.polylla_set_tuning(p.ctx, dict(t, relink_threads=96))
             polylla.polylla_capture_graph(p.ctx, stream)
@@ -146,7 +150,7 @@ def test_single_mesh_graph_and_tuning_keep_results():
             p.generate(stream)
             out = p.polygons(stream)
             stream.synchronize()
-            assert polylla.polylla_launch_count(p.ctx) == 10
+            assert polylla.polylla_launch_count(p.ctx) == 7
             assert np.array_equal(dm.next.cpu().numpy()[:3 * mesh.n_triangles], r.next_out[:3 * mesh.n_triangles])
             assert np.array_equal(out["he_list"].cpu().numpy(), r.he_list)
             assert np.array_equal(out["seeds"].cpu().numpy(), r.seeds)

@@ -202,8 +202,8 @@ def test_stage_timing_and_launch_count():
         polylla.polylla_set_timing(p.ctx, True)
         p.generate()
         t = polylla.polylla_get_stage_times(p.ctx)
-        assert list(t) == ["longest_edge", "label_relink", "chords", "chord_links", "cand_count",
-                           "cand_scan", "cand_write", "walk", "chunk_scan", "emit", "batch_pack", "batch_unpack"]
+        assert list(t) == ["longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan",
+                           "poly_list", "batch_pack", "batch_unpack"]
         assert all(v >= 0 for v in t.values())
         assert t["batch_pack"] == 0 and t["batch_unpack"] == 0
-        assert polylla.polylla_launch_count(p.ctx) == 10
+        assert polylla.polylla_launch_count(p.ctx) == 7

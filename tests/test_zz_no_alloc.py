@@ -1,19 +1,22 @@
 """polylla_generate_noalloc: the no-allocation entry point.
 
-It exists for callers that cannot call cudaMalloc (a serving loop that
-must not allocate once running, code recorded into a CUDA graph, a process
-whose device memory belongs to another allocator): the library keeps its
-scratch in one static device array, and the caller supplies the mesh and
-the output buffers.  These tests call it through the C ABI and check its
-result against the context-based entry point (polylla_create /
-polylla_generate / polylla_get_polygons), bit for bit, on two calls in a
-row.  The file name makes pytest collect it last.
+It exists for callers that cannot call cudaMalloc: a serving loop that must
+not allocate once it runs (an allocation can block on, or fail against,
+memory that other work holds), or a process whose device memory belongs to
+another allocator.  The library keeps the call's scratch in one static
+device array of fixed size, and the caller supplies the mesh and the output
+buffers.  These tests call it through the C ABI and check its result, bit
+for bit and on two calls in a row, against the context-based entry point
+(polylla_create / polylla_generate / polylla_get_polygons) and, on a mesh
+just under the array's limit with many barrier tips, against the oracle.
+The file name makes pytest collect it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2403_14723_gb300 import build, meshgen, polylla
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +36,13 @@ def _context_result(mesh):
     return res
 
 
+def _oracle_result(mesh):
+    r = oracle.run_mesh(mesh)
+    return {"seeds": r.seeds, "offsets": r.offsets, "he_list": r.he_list, "v_list": r.v_list,
+            "n_polygons": r.n_polygons, "n_frontier": int(r.he_list.shape[0]),
+            "next": r.next_out, "prev": r.prev_out, "tips": r.stats["tips"]}
+
+
 def _noalloc_call(lib, mesh, dm, outs, stream):
     T = mesh.n_triangles
     m = polylla.polylla_mesh(
@@ -47,15 +57,15 @@ def _noalloc_call(lib, mesh, dm, outs, stream):
     return rc
 
 
-def test_noalloc_matches_context_entry_point_twice():
+def _check_twice(mesh, want):
+    """Two no-allocation calls in a row on fresh output buffers filled with
+    junk, each compared with ``want`` array by array."""
     import torch
 
     build.build_library()
     lib = polylla.load_library()
-    mesh = meshgen.random_delaunay(4000, seed=31)     # ~7,970 triangles, with barrier tips
     T = mesh.n_triangles
     assert T <= polylla.POLYLLA_NOALLOC_MAX_TRIANGLES
-    want = _context_result(mesh)
     dm = polylla.DeviceMesh.from_host(mesh)
     stream = torch.cuda.current_stream()
     outs = {"seeds": torch.empty(T, dtype=torch.int32, device="cuda"),
@@ -79,6 +89,23 @@ def test_noalloc_matches_context_entry_point_twice():
         assert np.array_equal(dm.prev.cpu().numpy(), want["prev"])
 
 
+def test_noalloc_matches_context_entry_point_twice():
+    mesh = meshgen.random_delaunay(4000, seed=31)     # ~7,970 triangles, with barrier tips
+    _check_twice(mesh, _context_result(mesh))
+
+
+def test_noalloc_at_its_limit_matches_oracle_twice():
+    """A Delaunay mesh just under POLYLLA_NOALLOC_MAX_TRIANGLES: the static
+    label, tip and chord regions and the output tiles' look-back words are
+    used up to (nearly) their full size, with thousands of barrier tips."""
+    mesh = meshgen.random_delaunay(65_500, seed=33)
+    T = mesh.n_triangles
+    assert 0.99 * polylla.POLYLLA_NOALLOC_MAX_TRIANGLES < T <= polylla.POLYLLA_NOALLOC_MAX_TRIANGLES
+    want = _oracle_result(mesh)
+    assert want["tips"] > 1000
+    _check_twice(mesh, want)
+
+
 def test_noalloc_rejects_meshes_beyond_its_scratch():
     import torch
 
@@ -90,4 +117,4 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
     m = polylla.polylla_mesh(T + 2, T, 3 * T + 3, p, p, p, p, p)
     rc = lib.polylla_generate_noalloc(ctypes.byref(m), p, p, p, p, p, ctypes.c_void_p(0))
     assert rc == -8
-    assert lib.polylla_status_string(rc) == b"mesh larger than the no-allocation scratch"
+    assert lib.polylla_status_string(rc).startswith(b"mesh larger than the available capacity")
