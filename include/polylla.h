@@ -281,8 +281,10 @@ int polylla_capture_graph(polylla_ctx *ctx, polylla_stream stream);
 int polylla_release_graph(polylla_ctx *ctx);
 
 /*
- * Launch tuning (results never depend on it).  relink_threads is the block
- * size of the relink kernel (64, 128 or 256); longest_edge_blocks the grid
+ * Launch tuning (results never depend on it).  relink_tile is the triangles
+ * per CTA of the relink kernel and relink_items the triangles each of its
+ * threads labels and links: (64, 1), (128, 1), (256, 1), (256, 2) or
+ * (256, 4); longest_edge_blocks the grid
  * (blocks, in [1, 64 * SMs]) of the persistent longest-edge kernel;
  * output_tile the triangles per tile of the output kernel (1024, 2048 or
  * 4096) and output_items the triangles each of its threads walks and lists
@@ -297,7 +299,8 @@ int polylla_release_graph(polylla_ctx *ctx);
  * polylla_tuning_cache_clear empties the table.
  */
 typedef struct {
-    int32_t relink_threads;
+    int32_t relink_tile;
+    int32_t relink_items;
     int32_t longest_edge_blocks;
     int32_t output_tile;
     int32_t output_items;

@@ -250,10 +250,12 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
     k_longest_edge<<<blocks, LE_THREADS, 0, s>>>(m, w);
 }
 
+
 // ===========================================================================
 // Stages 2-4 fused: frontier labels (Algorithm 3 / 9), seeds (Algorithm 4 /
 // 10) and the relink of every frontier half-edge (Section 4.2; the per-half-
-// edge form of Algorithm 12), one thread per triangle for the labels.
+// edge form of Algorithm 12).  A CTA of NT threads takes NT * IPT
+// consecutive triangles, IPT per thread (strided: triangle t0 + q NT + tid).
 //
 //   F0[e] = border(e) or (not LE[e] and not LE[twin e])
 //   seed  = the triangle's longest half-edge e when it is the smaller half of
@@ -270,92 +272,100 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 // frontier array is needed.  Twin values are split into (triangle, corner)
 // once, so a rotation step costs one twin and one byte load, and the next
 // step's twin is fetched together with the current step's byte.
-// next and prev of the block are assembled in shared memory and stored
-// coalesced; only prev[x] for an x outside the block is stored directly.
+// next and prev of the CTA's triangles are assembled in shared memory and
+// stored coalesced; only prev[x] for an x outside them is stored directly.
 // In place is race-free: the rotation reads only twin and le; each next[e]
 // is written once (by e's thread, or by the lane that ran e's rotation) and
 // each prev[x] once, for the unique e with next[e] = x (or by x's own
 // thread when x is not frontier).
-// ===========================================================================
-__device__ __forceinline__ int32_t div3(int32_t x) { return (int32_t)((uint32_t)x / 3u); }
-
-// Rotations are compacted per warp.  Each thread labels its triangle and
+//
+// Rotations are compacted per warp.  Each thread labels its triangles and
 // links the frontier half-edges whose successor is the next half-edge of the
 // same triangle; the others (the successor lies across a non-frontier edge)
 // become tasks that the warp's lanes then take one each, so a warp runs its
-// rotations side by side instead of once per local half-edge.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
-    __shared__ __align__(16) int32_t s_nx[3 * NT];
-    __shared__ __align__(16) int32_t s_pv[3 * NT];
-    __shared__ int4 s_task[NT / 32][96];
-    const int32_t t0 = blockIdx.x * NT;
-    const int32_t nT = min(NT, m.T - t0);
+// rotations side by side instead of once per local half-edge.  (Staging the
+// CTA's twin and longest-edge bytes in shared memory by bulk copies measured
+// slower: on row-major grids half of each vertex fan lies in the next row,
+// outside any tile narrower than a row.)
+// ===========================================================================
+__device__ __forceinline__ int32_t div3(int32_t x) { return (int32_t)((uint32_t)x / 3u); }
+
+template <int NT, int IPT>
+__global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m, Work w) {
+    constexpr int TT = NT * IPT;  // triangles per CTA
+    static_assert(IPT >= 1 && IPT <= 4, "a thread's flag bytes fit one 32-bit word");
+    __shared__ __align__(16) int32_t s_nx[3 * TT];
+    __shared__ __align__(16) int32_t s_pv[3 * TT];
+    __shared__ int4 s_task[NT / 32][96 * IPT];
+    const int32_t t0 = blockIdx.x * TT;
+    const int32_t nT = min(TT, m.T - t0);
     const int32_t eb = 3 * t0;
     const int32_t nE = 3 * nT;
     const int32_t HI = 3 * m.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int32_t t = t0 + threadIdx.x;
-    const bool live = threadIdx.x < nT;
-    const int32_t e0 = 3 * t;
-    const int32_t lb = 3 * (int32_t)threadIdx.x;
-    uint32_t fl = 0, pend = 0;
-    int32_t tw[3], ttri[3];
-    uint32_t tloc[3], lnb[3];
-    if (live) {
-        tw[0] = __ldg(m.twin + e0);
-        tw[1] = __ldg(m.twin + e0 + 1);
-        tw[2] = __ldg(m.twin + e0 + 2);
-        const uint32_t lt = w.le[t];
-        uint32_t F = 0, twle = 0;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const bool b = tw[k] >= HI;
-            ttri[k] = b ? 0 : div3(tw[k]);
-            tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
-            lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
-            const bool tl = !b && lnb[k] == tloc[k];
-            F |= (uint32_t)(b || ((uint32_t)k != lt && !tl)) << k;
-            twle |= (uint32_t)tl << k;
-        }
-        const int32_t twl = lt == 0u ? tw[0] : (lt == 1u ? tw[1] : tw[2]);
-        const bool seed = (twl >= HI) || (((twle >> lt) & 1u) && (e0 + (int32_t)lt) < twl);
-        fl = F | ((uint32_t)seed << 6);
-        // own slots first: non-frontier half-edges keep their triangle
-        // links, frontier ones wait for their predecessor (-1 until then)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const int j = k == 2 ? 0 : k + 1;
-            const bool f = (F >> k) & 1u;
-            s_pv[lb + k] = f ? -1 : e0 + (k == 0 ? 2 : k - 1);
-            if (!f || ((F >> j) & 1u)) s_nx[lb + k] = e0 + j;
-            else pend |= 1u << k;
-        }
-    }
-    __syncthreads();
-    if (live) {
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const int j = k == 2 ? 0 : k + 1;
-            if (((fl >> k) & 1u) && ((fl >> j) & 1u)) s_pv[lb + j] = e0 + k;  // successor in the same triangle
-        }
-    }
-    // compact the warp's pending rotations, local edge by local edge (the
-    // order of the tasks does not matter: each writes its own slots)
     const uint32_t below = (1u << lane) - 1u;
+    uint32_t fls = 0;  // byte q: flags of triangle t0 + q NT + tid
     uint32_t total = 0;
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const bool mine = (pend >> k) & 1u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, mine);
-        if (mine) {
-            const int j = k == 2 ? 0 : k + 1;
-            s_task[wid][total + __popc(bal & below)] =
-                make_int4(e0 + k, tw[k], ttri[j], (int32_t)(tloc[j] | (lnb[j] << 2)));
+    for (int q = 0; q < IPT; q++) {
+        const int32_t lt = q * NT + (int32_t)threadIdx.x;
+        const bool live = lt < nT;
+        const int32_t t = t0 + lt;
+        const int32_t e0 = 3 * t;
+        const int32_t lb = 3 * lt;
+        uint32_t pend = 0;
+        int32_t tw[3], ttri[3];
+        uint32_t tloc[3], lnb[3];
+        if (live) {
+            tw[0] = __ldg(m.twin + e0);
+            tw[1] = __ldg(m.twin + e0 + 1);
+            tw[2] = __ldg(m.twin + e0 + 2);
+            const uint32_t ltl = w.le[t];
+            uint32_t F = 0, twle = 0;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const bool b = tw[k] >= HI;
+                ttri[k] = b ? 0 : div3(tw[k]);
+                tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
+                lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
+                const bool tl = !b && lnb[k] == tloc[k];
+                F |= (uint32_t)(b || ((uint32_t)k != ltl && !tl)) << k;
+                twle |= (uint32_t)tl << k;
+            }
+            const int32_t twl = ltl == 0u ? tw[0] : (ltl == 1u ? tw[1] : tw[2]);
+            const bool seed = (twl >= HI) || (((twle >> ltl) & 1u) && (e0 + (int32_t)ltl) < twl);
+            fls |= (F | ((uint32_t)seed << 6)) << (8 * q);
+            // own slots: non-frontier half-edges keep their triangle links,
+            // frontier ones wait for their predecessor (-1 until then)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int j = k == 2 ? 0 : k + 1;
+                const bool f = (F >> k) & 1u;
+                s_pv[lb + k] = f ? -1 : e0 + (k == 0 ? 2 : k - 1);
+                if (!f || ((F >> j) & 1u)) s_nx[lb + k] = e0 + j;
+                else pend |= 1u << k;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int j = k == 2 ? 0 : k + 1;
+                if (((F >> k) & 1u) && ((F >> j) & 1u)) s_pv[lb + j] = e0 + k;  // successor in the triangle
+            }
         }
-        total += __popc(bal);
+        // compact the warp's pending rotations (the order of the tasks does
+        // not matter: each writes its own slots)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const bool mine = (pend >> k) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+                const int j = k == 2 ? 0 : k + 1;
+                s_task[wid][total + __popc(bal & below)] =
+                    make_int4(e0 + k, tw[k], ttri[j], (int32_t)(tloc[j] | (lnb[j] << 2)));
+            }
+            total += __popc(bal);
+        }
     }
-    __syncwarp();
+    __syncthreads();  // every slot initialised before the rotations write prev
     for (uint32_t i = lane; i < total; i += 32) {
         const int4 tk = s_task[wid][i];
         const int32_t e = tk.x;
@@ -395,22 +405,28 @@ __global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
         }
     }
     __syncthreads();
-    if (live) {
+    // walk-start marks: frontier, next and prev larger (prev unknown: set
+    // by another CTA, counted as larger)
+#pragma unroll
+    for (int q = 0; q < IPT; q++) {
+        const int32_t lt = q * NT + (int32_t)threadIdx.x;
+        if (lt >= nT) break;
+        uint32_t fl = (fls >> (8 * q)) & 0xffu;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const int32_t e = e0 + k;
-            const int32_t pv = s_pv[lb + k];
-            if (((fl >> k) & 1u) && s_nx[lb + k] > e && (pv < 0 || pv > e)) fl |= 8u << k;
+            const int32_t e = eb + 3 * lt + k;
+            const int32_t pv = s_pv[3 * lt + k];
+            if (((fl >> k) & 1u) && s_nx[3 * lt + k] > e && (pv < 0 || pv > e)) fl |= 8u << k;
         }
-        w.flags[t] = (uint8_t)fl;
+        w.flags[t0 + lt] = (uint8_t)fl;
     }
     int4 *dn = reinterpret_cast<int4 *>(m.next + eb);
     for (int i = threadIdx.x; 4 * i < nE; i += NT) {
         if (4 * i + 3 < nE) {
             dn[i] = reinterpret_cast<const int4 *>(s_nx)[i];
         } else {
-            for (int q = 0; q < 4; q++)
-                if (4 * i + q < nE) m.next[eb + 4 * i + q] = s_nx[4 * i + q];
+            for (int c = 0; c < 4; c++)
+                if (4 * i + c < nE) m.next[eb + 4 * i + c] = s_nx[4 * i + c];
         }
     }
     for (int i = threadIdx.x; i < nE; i += NT) {
@@ -419,12 +435,33 @@ __global__ void __launch_bounds__(NT) k_label_relink(MeshView m, Work w) {
     }
 }
 
+// launch configurations: (triangles per CTA, triangles per thread)
+#define RELINK_CONFIGS(X) \
+    X(64, 1)              \
+    X(128, 1)             \
+    X(256, 1)             \
+    X(128, 2)             \
+    X(64, 4)
+
+bool relink_config_valid(int32_t tile, int32_t items) {
+#define X(N, I) \
+    if (tile == N * I && items == I) return true;
+    RELINK_CONFIGS(X)
+#undef X
+    return false;
+}
+
+int relink_configure() { return 0; }  // static shared memory only
+
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
-    switch (w.rl_threads) {
-        case 64: k_label_relink<64><<<(m.T + 63) / 64, 64, 0, s>>>(m, w); break;
-        case 256: k_label_relink<256><<<(m.T + 255) / 256, 256, 0, s>>>(m, w); break;
-        default: k_label_relink<128><<<(m.T + 127) / 128, 128, 0, s>>>(m, w); break;
+#define X(N, I)                                                                      \
+    if (w.rl_tile == N * I && w.rl_items == I) {                                     \
+        k_label_relink<N, I><<<(m.T + N * I - 1) / (N * I), N, 0, s>>>(m, w);        \
+        return;                                                                      \
     }
+    RELINK_CONFIGS(X)
+#undef X
+    k_label_relink<128, 1><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
 }
 
 }  // namespace polylla

@@ -158,13 +158,14 @@ static int sm_count(polylla_ctx *c) {
 
 static bool tuning_valid(polylla_ctx *c, const polylla_tuning &t) {
     const int cap = 64 * sm_count(c);
-    return (t.relink_threads == 64 || t.relink_threads == 128 || t.relink_threads == 256) &&
+    return relink_config_valid(t.relink_tile, t.relink_items) &&
            t.longest_edge_blocks >= 1 && t.longest_edge_blocks <= cap &&
            polygons_config_valid(t.output_tile, t.output_items);
 }
 
 static void apply_tuning(polylla_ctx *c, const polylla_tuning &t) {
-    c->w.rl_threads = t.relink_threads;
+    c->w.rl_tile = t.relink_tile;
+    c->w.rl_items = t.relink_items;
     c->w.le_blocks = t.longest_edge_blocks;
     c->w.out_tile = t.output_tile;
     c->w.out_items = t.output_items;
@@ -172,7 +173,8 @@ static void apply_tuning(polylla_ctx *c, const polylla_tuning &t) {
 
 static polylla_tuning current_tuning(const polylla_ctx *c) {
     polylla_tuning t;
-    t.relink_threads = c->w.rl_threads;
+    t.relink_tile = c->w.rl_tile;
+    t.relink_items = c->w.rl_items;
     t.longest_edge_blocks = c->w.le_blocks;
     t.output_tile = c->w.out_tile;
     t.output_items = c->w.out_items;
@@ -242,8 +244,9 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
     c->w.out_tile = OUT_TILE_DEFAULT;
     c->w.out_items = OUT_ITEMS_DEFAULT;
-    c->w.rl_threads = RL_THREADS;
-    if (polygons_configure() != 0) return cuda_fail(c, cudaGetLastError());
+    c->w.rl_tile = RL_TILE_DEFAULT;
+    c->w.rl_items = RL_ITEMS_DEFAULT;
+    if (polygons_configure() != 0 || relink_configure() != 0) return cuda_fail(c, cudaGetLastError());
     c->w.max_rot = (opt && opt->max_rotation > 0) ? opt->max_rotation : 4096;
     apply_cached_tuning(c);
     for (int i = 0; i < kStages; i++) {
@@ -755,10 +758,14 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
         int n = 0;
         const polylla_tuning cur = current_tuning(c);
         if (q == 0) {
-            for (int32_t v : {64, 128, 256}) {
-                cand[n] = cur;
-                cand[n++].relink_threads = v;
-            }
+            // relink tile and triangles per thread
+            const int32_t pairs[][2] = {{64, 1}, {128, 1}, {256, 1}, {256, 2}, {256, 4}};
+            for (const auto &pr : pairs)
+                if (relink_config_valid(pr[0], pr[1])) {
+                    cand[n] = cur;
+                    cand[n].relink_tile = pr[0];
+                    cand[n++].relink_items = pr[1];
+                }
         } else if (q == 1) {
             for (int k = 1; k <= le_occ && n < 8; k++) {
                 cand[n] = cur;

@@ -63,7 +63,8 @@ struct Work {
     int32_t n_tile_max;             // ceil(T / OUT_TILE_MIN)
     int32_t out_tile;               // output tile: triangles
     int32_t out_items;              // output kernel: triangles per thread
-    int32_t rl_threads;             // relink block size: 64, 128 or 256
+    int32_t rl_tile;                // relink: triangles per CTA
+    int32_t rl_items;               // relink: triangles per thread
     int32_t *seeds;
     int32_t *offsets;
     int32_t *he_list;
@@ -114,8 +115,9 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int LE_THREADS = 256;
 constexpr int LE_TILE = 64;
 
-// relink kernel: one thread per triangle, 64, 128 (default) or 256 per block
-constexpr int RL_THREADS = 128;
+// relink kernel: rl_tile triangles per CTA, rl_items per thread
+constexpr int RL_TILE_DEFAULT = 128;
+constexpr int RL_ITEMS_DEFAULT = 1;
 
 // bounded waits: iterations of an mbarrier try_wait loop before giving up
 constexpr int MBAR_WAIT_LIMIT = 1 << 22;
@@ -194,6 +196,10 @@ void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s);
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s);
 int longest_edge_blocks_per_sm();
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
+// allows the relink kernels their shared memory on the current device (once
+// per device before the first launch); 0 on success
+int relink_configure();
+bool relink_config_valid(int32_t tile, int32_t items);
 void launch_chords(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s);

@@ -52,8 +52,8 @@ static unsigned char *g_scratch_addr[kMaxDevices];  // device address per device
 static int g_sms[kMaxDevices];
 
 // Set-up, once per device, on the current device (the first call there):
-// look up the scratch array's device address, allow the output kernel its
-// shared memory, read the SM count.
+// look up the scratch array's device address, allow the relink and output
+// kernels their shared memory, read the SM count.
 static int device_setup(unsigned char **out, int *sms) {
     int d = 0;
     if (cudaGetDevice(&d) != cudaSuccess) return POLYLLA_ERR_CUDA;
@@ -63,7 +63,7 @@ static int device_setup(unsigned char **out, int *sms) {
         void *p = nullptr;
         int n = 0;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return POLYLLA_ERR_CUDA;
-        if (polygons_configure() != 0) return POLYLLA_ERR_CUDA;
+        if (polygons_configure() != 0 || relink_configure() != 0) return POLYLLA_ERR_CUDA;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) return POLYLLA_ERR_CUDA;
         g_sms[d] = n > 0 ? n : 1;
         g_scratch_addr[d] = static_cast<unsigned char *>(p);
@@ -125,7 +125,8 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.le_blocks = longest_edge_blocks_per_sm() * sms;
     w.out_tile = OUT_TILE_DEFAULT;
     w.out_items = OUT_ITEMS_DEFAULT;
-    w.rl_threads = RL_THREADS;
+    w.rl_tile = RL_TILE_DEFAULT;
+    w.rl_items = RL_ITEMS_DEFAULT;
 
     // The first kernel zeroes the control block (counters) and the output
     // tiles' totals; every other scratch word is written
