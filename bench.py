@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single mesh only: no batched and served sub-records in the default line")
+    ap.add_argument("--extras-serve-seconds", type=float, default=10.0,
+                    help="served sub-record: length of the request trace")
+    ap.add_argument("--extras-serve-baseline-seconds", type=float, default=5.0,
+                    help="served sub-record: trace length through the one-mesh-at-a-time server")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch settings (profiling runs: no tuning launches before the steps)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
@@ -324,6 +330,11 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_gb300(args):
+    # the batched and served workloads' host meshes are built meanwhile, in
+    # spawned processes (single-GPU runs of the default workload only)
+    bg = None
+    if args.workload == "pgrid_4096" and not args.no_extras and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        bg = BackgroundPools(BATCH_RECIPE["meshes"])
     import numpy as np
     import torch
 
@@ -485,6 +496,59 @@ def run_gb300(args):
                             "api": f"polylla_server_replay of {e_steps} requests of the mesh, all arriving at once"}
         del hr
 
+    polylla.polylla_destroy(ctx)
+    clocks = clk.summary()
+    del dm
+
+    # ---- batched and served sub-records (same process, same GPU) --------
+    batched = served = None
+    if bg is not None:
+        meshes, gen_b = bg.batch()
+        bctx, bdb, b = measure_batched(meshes, max(10, min(args.steps, 50)), args.warmup, dev, ws, local,
+                                       clock=False)
+        polylla.polylla_destroy(bctx)
+        del bdb
+        r = BATCH_RECIPE
+        batched = {
+            "workload": f"batch_{len(meshes)}", "meshes": len(meshes), "triangles": b["T"],
+            "polygons": b["P"], "frontier_halfedges": b["NF"],
+            "sizes": f"log-uniform [{r['t_min']}, {r['t_max']}] triangles, seed {r['seed']}; "
+                     "even meshes Delaunay of uniform points, odd perturbed grids (jitter 0.3)",
+            "value": b["T"] / (b["ms"] * 1e-3), "unit": UNIT, "ms_per_step": b["ms"],
+            "steps": max(10, min(args.steps, 50)), "cuda_graph": True, "whole_step": b["whole_step"],
+            "stage_ms": b["stage_ms"], "tuning": b["tuning"], "gpu_launches": b["launches"],
+            "without_graph": {"value": b["T"] / (b["ms_nograph"] * 1e-3), "ms_per_step": b["ms_nograph"]},
+            "one_mesh_at_a_time": {"value": b["T"] / (b["ms_loop"] * 1e-3), "unit": UNIT,
+                                   "ms_per_step": b["ms_loop"], "launches_per_step": b["launches_loop"],
+                                   "how": "polylla_generate per mesh, back to back on one stream"},
+            "l2": f"256 MiB buffer written between timed steps; inputs {(16 * b['V'] + 16 * b['H']) / 1e9:.2f} GB",
+            "host_generation_s": gen_b,
+        }
+        del meshes
+        small, large, gen_s = bg.serve()
+        bg.close()
+        sv = measure_served(small, large, args.extras_serve_seconds, args.extras_serve_baseline_seconds,
+                            args.serve_slots, args.serve_batch_triangles, args.serve_lane, rank, ws, local)
+        m_, b_, st = sv["main"], sv["base"], sv["stats"]
+        rs = SERVE_RECIPE
+        served = {
+            "workload": "served", "rate_req_per_s": rs["rate"], "seconds": args.extras_serve_seconds,
+            "requests": m_["requests"], "triangles": m_["triangles"],
+            "value": sv["value"], "unit": UNIT, "latency_ms": {"p50": m_["p50_ms"], "p99": m_["p99_ms"]},
+            "queue_ms": m_["queue_ms"], "service_ms": m_["service_ms"], "mean_batch": m_["mean_batch"],
+            "batches": sv["batches"], "gpu_launches": sv["launches"], "batch_trace": m_["batch_trace"],
+            "mix": f"{int(100 * (1 - rs['p_large']))}% log-uniform {rs['small']} triangles, "
+                   f"{int(100 * rs['p_large'])}% log-uniform {rs['large']}; Delaunay and perturbed grids",
+            "pool": f"{len(small)} small + {len(large)} large seeded meshes in pinned host memory",
+            "memory_budget_bytes": rs["budget"], "slots": st["n_slots"], "lane_triangles": st["lane_triangles"],
+            "one_mesh_at_a_time": {"value": b_["tri_per_s"], "unit": UNIT, "seconds": args.extras_serve_baseline_seconds,
+                                   "requests": b_["requests"],
+                                   "latency_ms": {"p50": b_["p50_ms"], "p99": b_["p99_ms"]},
+                                   "how": "same server loop with one slot and one mesh per batch, same recipe"},
+            "copy_check": sv["copy_check"], "clocks": sv["clocks"], "host_generation_s": gen_s,
+        }
+        del small, large
+
     # ---- CPU baseline: the oracle, bounded sample, rank 0, N = 1 only -----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -503,8 +567,7 @@ def run_gb300(args):
                "sample": f"{sample}; median of 3 single-threaded runs (1 of {os.cpu_count()} host cores)",
                "stage_ms": {k: 1e3 * v for k, v in med_stages.items()}, "host": host_info()}
 
-    polylla.polylla_destroy(ctx)
-    clocks = clk.summary()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -516,6 +579,7 @@ def run_gb300(args):
                        "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
                              f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "lepp": lepp,
+            "batched": batched, "served": served,
             "gpu_launches": launches, "clocks": clocks,
             "kernel_digest": kernel_digest(), "core_kernel_digest": core_kernel_digest(),
         }
@@ -542,26 +606,25 @@ def batch_meshes(n_meshes: int):
     return meshgen.random_batch(n_meshes, r["t_min"], r["t_max"], r["seed"], workers=workers)
 
 
-def run_batched(args):
-    n_meshes = int(args.workload.split("_")[1])
-    meshes = batch_meshes(n_meshes)        # process pool, before any CUDA call
+def measure_batched(meshes, steps: int, warmup: int, dev, ws: int, local: int, clock: bool = True):
+    """The batched mode on ``meshes``: autotuned, one CUDA graph launch per
+    step, timed with CUDA events (L2 flushed between steps), beside the
+    plain one-mesh-at-a-time path on the same meshes.  Returns the batch
+    context (still alive, for the end-to-end leg), its device batch, and a
+    dict of the measurements."""
     import numpy as np
     import torch
 
-    from paper_2403_14723_gb300 import build, polylla
+    from paper_2403_14723_gb300 import polylla
 
-    rank, ws, local = dist_setup(args.gpus)
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    build.build_library()
+    n_meshes = len(meshes)
     db = polylla.DeviceBatch.from_host(meshes, device=dev)
     T = int(db.triangle_offset[-1])
     V = int(db.vertex_offset[-1])
     H = int(db.halfedge_offset[-1])
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    res = {}
     with torch.cuda.stream(stream):
         ctx = polylla.polylla_batch_create(db, stream=stream)
         tuning = polylla.polylla_autotune(ctx, reps=3, stream=stream)
@@ -594,17 +657,21 @@ def run_batched(args):
 
         for _ in range(3):
             step()
-        ms_nograph = timed(max(3, min(args.steps, 20)), step)
+        ms_nograph = timed(max(3, min(steps, 20)), step)
         polylla.polylla_capture_graph(ctx, stream)
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             step()
         stream.synchronize()
         dist_barrier(ws)
-        with ClockSampler(local) as clk:
-            ms = timed(args.steps, step)
+        if clock:
+            with ClockSampler(local) as clk:
+                ms = timed(steps, step)
+            res["clocks"] = clk.summary()
+        else:
+            ms = timed(steps, step)
         dist_barrier(ws)
         ms = dist_max(ms, ws)
-        launches = args.steps * polylla.polylla_launch_count(ctx)
+        launches = steps * polylla.polylla_launch_count(ctx)
         out = polylla.polylla_get_polygons(ctx, stream)
         P, NF = out["n_polygons"], out["n_frontier"]
         po = polylla.polylla_batch_polygon_offsets(ctx, n_meshes).cpu().numpy()
@@ -621,10 +688,40 @@ def run_batched(args):
         ms_loop = dist_max(timed(3, loop), ws)
         p_loop = [polylla.polylla_get_polygons(c, stream)["n_polygons"] for c in ctxs]
         assert np.array_equal(np.diff(po), np.array(p_loop)), "batched and per-mesh polygon counts differ"
+        launches_loop = sum(polylla.polylla_launch_count(c) for c in ctxs)
         for c in ctxs:
             polylla.polylla_destroy(c)
         del dms
+    total_alg, per_stage = algorithmic_bytes(T, V, NF, P)
+    peak, peak_kind = measured_peaks()
+    res.update({"T": T, "V": V, "H": H, "P": P, "NF": NF, "ms": ms, "ms_nograph": ms_nograph, "ms_loop": ms_loop,
+                "launches_loop": launches_loop, "stage_ms": stage_ms, "tuning": tuning, "launches": launches,
+                "stream": stream, "flush": flush,
+                "whole_step": {"algorithmic_bytes": total_alg, "achieved": total_alg / (ms * 1e-3) / 1e9,
+                               "frac": total_alg / (ms * 1e-3) / 1e9 / peak, "peak_source": f"{peak_kind} hbm_gbs"}})
+    return ctx, db, res
 
+
+def run_batched(args):
+    n_meshes = int(args.workload.split("_")[1])
+    meshes = batch_meshes(n_meshes)        # process pool, before any CUDA call
+    import numpy as np
+    import torch
+
+    from paper_2403_14723_gb300 import build, polylla
+
+    rank, ws, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build_library()
+    ctx, db, res = measure_batched(meshes, args.steps, args.warmup, dev, ws, local)
+    T, V, H, P, NF = res["T"], res["V"], res["H"], res["P"], res["NF"]
+    ms, ms_nograph, ms_loop = res["ms"], res["ms_nograph"], res["ms_loop"]
+    stage_ms, tuning, launches = res["stage_ms"], res["tuning"], res["launches"]
+    stream = res["stream"]
+    with torch.cuda.stream(stream):
         # ---- end to end: host arrays in, CSR and links out, copies timed ---
         e2e = None
         if not args.no_e2e:
@@ -690,7 +787,7 @@ def run_batched(args):
         cpu = {"value": sum(m.n_triangles for m in sample) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the first {len(sample)} meshes of the batch "
                          f"({sum(m.n_triangles for m in sample):,} triangles), one pass, single-threaded"}
-    clocks = clk.summary()
+    clocks = res.get("clocks")
     if rank == 0:
         r = BATCH_RECIPE
         line = {
@@ -705,7 +802,7 @@ def run_batched(args):
                        "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
                              f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "one_mesh_at_a_time": {"value": ws * T / (ms_loop * 1e-3), "unit": UNIT, "ms_per_step": ms_loop,
-                                   "launches_per_step": 10 * n_meshes,
+                                   "launches_per_step": res["launches_loop"],
                                    "how": "polylla_generate per mesh, back to back on one stream"},
             "without_graph": {"value": ws * T / (ms_nograph * 1e-3), "unit": UNIT, "ms_per_step": ms_nograph},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -727,23 +824,30 @@ SERVE_RECIPE = {"rate": 2000.0, "small": (1_000, 50_000), "large": (500_000, 8_0
                 "pool_small": 512, "pool_large": 32, "budget": 40 << 30, "seed": 5}
 
 
-def serve_pool():
-    """Seeded pool of request meshes: sizes log-uniform per band, Delaunay
-    and perturbed grids alternately (built in a spawned process pool)."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-
+def serve_pool_args():
+    """Arguments of meshgen's batch-member builder for the request pool:
+    sizes log-uniform per band, Delaunay and perturbed grids alternately."""
     from paper_2403_14723_gb300 import meshgen
 
     r = SERVE_RECIPE
     small = meshgen.batch_sizes(r["pool_small"], *r["small"], seed=r["seed"])
     large = meshgen.batch_sizes(r["pool_large"], *r["large"], seed=r["seed"] + 1)
-    args = [(i, int(t), 10_000 + r["seed"]) for i, t in enumerate(small)]
-    args += [(i, int(t), 20_000 + r["seed"]) for i, t in enumerate(large)]
+    return ([(i, int(t), 10_000 + r["seed"]) for i, t in enumerate(small)],
+            [(i, int(t), 20_000 + r["seed"]) for i, t in enumerate(large)])
+
+
+def serve_pool():
+    """Seeded pool of request meshes (built in a spawned process pool)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from paper_2403_14723_gb300 import meshgen
+
+    small_args, large_args = serve_pool_args()
     workers = max(1, min(16, os.cpu_count() or 1))
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
-        meshes = list(ex.map(meshgen._batch_member_args, args, chunksize=4))
-    return meshes[: len(small)], meshes[len(small):]
+        ms = list(ex.map(meshgen._batch_member_args, small_args + large_args, chunksize=4))
+    return ms[: len(small_args)], ms[len(small_args):]
 
 
 def serve_trace(seconds: float, n_small: int, n_large: int, seed: int):
@@ -821,25 +925,24 @@ def host_info() -> dict:
     return info
 
 
-def run_served(args):
-    small, large = serve_pool()               # process pool, before any CUDA call
+def measure_served(small, large, seconds: float, base_seconds: float, slots: int, batch_tri: int, lane: int,
+                   rank: int, ws: int, local: int):
+    """A Poisson request trace of the served recipe through the serving loop
+    (continuous batching), and the same loop with one slot and one mesh per
+    batch (the plain one-mesh-at-a-time GPU path) on a trace of the same
+    recipe.  Returns a dict of the measurements."""
     import numpy as np
     import torch
 
-    from paper_2403_14723_gb300 import build, polylla
+    from paper_2403_14723_gb300 import polylla
 
-    rank, ws, local = dist_setup(args.gpus)
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
-    torch.cuda.set_device(torch.device("cuda", local))
-    build.build_library()
     pool = small + large
     hrs = [polylla.HostRequest(m) for m in pool]
     tri = np.array([m.n_triangles for m in pool], dtype=np.int64)
     r = SERVE_RECIPE
 
-    def replay(srv, seconds, seed):
-        t, pick = serve_trace(seconds, len(small), len(large), seed)
+    def replay(srv, secs, seed):
+        t, pick = serve_trace(secs, len(small), len(large), seed)
         rc, lat, infos = srv.replay([hrs[i] for i in pick], t)
         assert rc == 0, f"served requests failed: {polylla.STATUS.get(rc, rc)}"
         span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
@@ -872,19 +975,17 @@ def run_served(args):
     copy_check = {"bytes": nbytes, "h2d_gbs": nbytes / (ev[0].elapsed_time(ev[1]) * 1e6),
                   "d2h_gbs": nbytes / (ev[1].elapsed_time(ev[2]) * 1e6)}
     del dev
-    with polylla.Server(memory_budget=r["budget"], n_slots=args.serve_slots,
-                        max_batch_triangles=args.serve_batch_triangles, lane_triangles=args.serve_lane) as srv:
+    with polylla.Server(memory_budget=r["budget"], n_slots=slots,
+                        max_batch_triangles=batch_tri, lane_triangles=lane) as srv:
         replay(srv, 1.0, seed=1000 + rank)                     # warm-up, untimed
         dist_barrier(ws)
         st0 = srv.stats()
         with ClockSampler(local) as clk:
-            main = replay(srv, args.serve_seconds, seed=r["seed"] + rank)
+            main = replay(srv, seconds, seed=r["seed"] + rank)
         st = srv.stats()
-    batches = int(st["batches"] - st0["batches"])
-    launches = int(st["launches"] - st0["launches"])
     with polylla.Server(memory_budget=r["budget"], n_slots=1, max_batch_meshes=1, lane_triangles=-1) as one:
         replay(one, 0.5, seed=2000 + rank)
-        base = replay(one, args.serve_baseline_seconds, seed=r["seed"] + rank)
+        base = replay(one, base_seconds, seed=r["seed"] + rank)
     value = main["tri_per_s"]
     if ws > 1:
         import torch.distributed as dist
@@ -892,6 +993,27 @@ def run_served(args):
         tot = torch.tensor([float(main["triangles"])], dtype=torch.float64, device="cuda")
         dist.all_reduce(tot)
         value = float(tot[0]) / dist_max(main["span_s"], ws)
+    del hrs
+    return {"main": main, "base": base, "value": value, "stats": st, "copy_check": copy_check,
+            "batches": int(st["batches"] - st0["batches"]), "launches": int(st["launches"] - st0["launches"]),
+            "clocks": clk.summary()}
+
+
+def run_served(args):
+    small, large = serve_pool()               # process pool, before any CUDA call
+    import torch
+
+    from paper_2403_14723_gb300 import build
+
+    rank, ws, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(torch.device("cuda", local))
+    build.build_library()
+    res = measure_served(small, large, args.serve_seconds, args.serve_baseline_seconds, args.serve_slots,
+                         args.serve_batch_triangles, args.serve_lane, rank, ws, local)
+    main, base, st, value = res["main"], res["base"], res["stats"], res["value"]
+    r = SERVE_RECIPE
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": main["requests"], "warmup": 1,
@@ -908,14 +1030,14 @@ def run_served(args):
                        "slot_triangles": st["slot_triangles"], "device_bytes": st["device_bytes"],
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": main["p50_ms"], "p99": main["p99_ms"]},
-            "served": main, "server_stats": st, "copy_check": copy_check, "batches": batches,
+            "served": main, "server_stats": st, "copy_check": res["copy_check"], "batches": res["batches"],
             "one_mesh_at_a_time": dict(base, how="same server loop with one slot and one mesh per batch, "
                                                   f"{args.serve_baseline_seconds:g} s of the same recipe"),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": main["h2d_bytes"] // max(1, main["requests"]),
                     "d2h_bytes_per_step": main["d2h_bytes"] // max(1, main["requests"]),
                     "api": "polylla_server_replay: host meshes in, host results out, per request"},
             "roofline": None, "cpu_baseline": None,
-            "gpu_launches": launches, "clocks": clk.summary(), "kernel_digest": kernel_digest(),
+            "gpu_launches": res["launches"], "clocks": res["clocks"], "kernel_digest": kernel_digest(),
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -923,6 +1045,42 @@ def run_served(args):
 
         dist.destroy_process_group()
     return 0
+
+
+class BackgroundPools:
+    """The batched workload's meshes and the served workload's request pool,
+    built in a spawned process pool while the caller measures the single
+    mesh on the GPU (spawned workers hold no CUDA state)."""
+
+    def __init__(self, n_batch: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        from paper_2403_14723_gb300 import meshgen
+
+        workers = max(1, min(16, (os.cpu_count() or 2) - 2))
+        self.t0 = time.perf_counter()
+        self.ex = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+        rb = BATCH_RECIPE
+        bsizes = meshgen.batch_sizes(n_batch, rb["t_min"], rb["t_max"], rb["seed"])
+        self.n_batch = n_batch
+        self.batch_it = self.ex.map(meshgen._batch_member_args, [(i, int(t), rb["seed"]) for i, t in enumerate(bsizes)],
+                                    chunksize=16)
+        small_args, large_args = serve_pool_args()
+        self.n_small = len(small_args)
+        self.serve_it = self.ex.map(meshgen._batch_member_args, small_args + large_args, chunksize=4)
+        self.workers = workers
+
+    def batch(self):
+        meshes = list(self.batch_it)
+        return meshes, time.perf_counter() - self.t0
+
+    def serve(self):
+        ms = list(self.serve_it)
+        return ms[: self.n_small], ms[self.n_small:], time.perf_counter() - self.t0
+
+    def close(self):
+        self.ex.shutdown(wait=True)
 
 
 def main():

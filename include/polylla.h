@@ -284,9 +284,9 @@ int polylla_release_graph(polylla_ctx *ctx);
  * Launch tuning (results never depend on it).  relink_tile is the triangles
  * per CTA of the relink kernel and relink_items the triangles each of its
  * threads labels and links: (64, 1), (128, 1), (256, 1), (256, 2) or
- * (256, 4); longest_edge_blocks the grid
- * (blocks, in [1, 64 * SMs]) of the persistent longest-edge kernel;
- * output_tile the triangles per tile of the output kernel (1024, 2048 or
+ * (256, 4); longest_edge_items the triangles per lane of the persistent
+ * longest-edge kernel (2 or 4) and longest_edge_blocks its grid (blocks,
+ * in [1, 64 * SMs]); output_tile the triangles per tile of the output kernel (1024, 2048 or
  * 4096) and output_items the triangles each of its threads walks and lists
  * (4 or 8; a tile of 4096 with 4 per thread is a block of 1024 threads).
  * polylla_autotune times whole generates (reps per setting, median of the
@@ -302,6 +302,7 @@ typedef struct {
     int32_t relink_tile;
     int32_t relink_items;
     int32_t longest_edge_blocks;
+    int32_t longest_edge_items;
     int32_t output_tile;
     int32_t output_items;
 } polylla_tuning;

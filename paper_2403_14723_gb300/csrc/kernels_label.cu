@@ -159,15 +159,18 @@ __device__ __forceinline__ uint32_t longest_of(double2 p0, double2 p1, double2 p
     return k;
 }
 
-// Persistent warps walk 64-triangle tiles.  Each warp owns a two-stage
-// shared-memory ring: lane 0 bulk-copies (TMA engine, cp.async.bulk +
-// mbarrier) the origin triples of the warp's next tile while the warp
-// computes the current one, so the HBM stream of origin never waits on the
-// coordinate gathers and no warp waits for another (no block barrier).
-// Each lane takes 2 triangles (lane and lane + 32, so a warp's gathers and
-// byte stores stay contiguous) and issues their 6 coordinate loads together.
+// Persistent warps walk tiles of 32 PER triangles.  Each warp owns a
+// two-stage shared-memory ring: lane 0 bulk-copies (TMA engine,
+// cp.async.bulk + mbarrier) the origin triples of the warp's next tile while
+// the warp computes the current one, so the HBM stream of origin never waits
+// on the coordinate gathers and no warp waits for another (no block
+// barrier).  Each lane takes PER triangles (lane, lane + 32, ..., so a
+// warp's gathers and byte stores stay contiguous) and issues their 3 PER
+// coordinate loads together.
+template <int PER>
 __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w) {
     constexpr int NW = LE_THREADS / 32;
+    constexpr int LE_TILE = 32 * PER;
     __shared__ __align__(128) int32_t s_org[NW][2][3 * LE_TILE];
     __shared__ __align__(8) uint64_t s_bar[NW][2];
     // reset this generate's control block (error word, tip count, totals)
@@ -199,7 +202,6 @@ __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w)
     int32_t tile = blockIdx.x * NW + warp;
     if (lane == 0 && tile < n_tiles) issue(tile, 0);
     uint32_t parity = 0u;  // bit st = parity to wait for on stage st
-    constexpr int PER = LE_TILE / 32;
     for (int it = 0; tile < n_tiles; it++, tile += nwarps) {
         const int st = it & 1;
         const int32_t nxt = tile + nwarps;
@@ -236,18 +238,23 @@ __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w)
     }
 }
 
-int longest_edge_blocks_per_sm() {
+int longest_edge_blocks_per_sm(int32_t items) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_longest_edge, LE_THREADS, 0) != cudaSuccess) n = 1;
+    const cudaError_t e = items == 4
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_longest_edge<4>, LE_THREADS, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_longest_edge<2>, LE_THREADS, 0);
+    if (e != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
 
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
-    const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;
+    const int32_t tile = 32 * (w.le_items == 4 ? 4 : 2);
+    const int32_t n_tiles = (m.T + tile - 1) / tile;
     const int32_t want = (n_tiles + LE_THREADS / 32 - 1) / (LE_THREADS / 32);  // one tile per warp
     const int blocks = want < w.le_blocks ? want : w.le_blocks;
     // the control-block reset needs >= 8 threads: any grid >= 1 works
-    k_longest_edge<<<blocks, LE_THREADS, 0, s>>>(m, w);
+    if (w.le_items == 4) k_longest_edge<4><<<blocks, LE_THREADS, 0, s>>>(m, w);
+    else k_longest_edge<2><<<blocks, LE_THREADS, 0, s>>>(m, w);
 }
 
 

@@ -160,6 +160,7 @@ static bool tuning_valid(polylla_ctx *c, const polylla_tuning &t) {
     const int cap = 64 * sm_count(c);
     return relink_config_valid(t.relink_tile, t.relink_items) &&
            t.longest_edge_blocks >= 1 && t.longest_edge_blocks <= cap &&
+           (t.longest_edge_items == 2 || t.longest_edge_items == 4) &&
            polygons_config_valid(t.output_tile, t.output_items);
 }
 
@@ -167,6 +168,7 @@ static void apply_tuning(polylla_ctx *c, const polylla_tuning &t) {
     c->w.rl_tile = t.relink_tile;
     c->w.rl_items = t.relink_items;
     c->w.le_blocks = t.longest_edge_blocks;
+    c->w.le_items = t.longest_edge_items;
     c->w.out_tile = t.output_tile;
     c->w.out_items = t.output_items;
 }
@@ -176,6 +178,7 @@ static polylla_tuning current_tuning(const polylla_ctx *c) {
     t.relink_tile = c->w.rl_tile;
     t.relink_items = c->w.rl_items;
     t.longest_edge_blocks = c->w.le_blocks;
+    t.longest_edge_items = c->w.le_items;
     t.output_tile = c->w.out_tile;
     t.output_items = c->w.out_items;
     return t;
@@ -241,7 +244,8 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
-    c->w.le_blocks = longest_edge_blocks_per_sm() * (sms > 0 ? sms : 1);
+    c->w.le_items = LE_ITEMS_DEFAULT;
+    c->w.le_blocks = longest_edge_blocks_per_sm(LE_ITEMS_DEFAULT) * (sms > 0 ? sms : 1);
     c->w.out_tile = OUT_TILE_DEFAULT;
     c->w.out_items = OUT_ITEMS_DEFAULT;
     c->w.rl_tile = RL_TILE_DEFAULT;
@@ -749,7 +753,6 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
     };
     // one knob per stage, tried in stage order: its candidates are whole
     // tunings that differ from the current one in that knob's fields only
-    const int le_occ = longest_edge_blocks_per_sm();
     int rc = POLYLLA_OK;
     for (int q = 0; q < 3 && !rc; q++) {
         // relink, longest edge, the output kernels (count, scan, list)
@@ -767,9 +770,14 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
                     cand[n++].relink_items = pr[1];
                 }
         } else if (q == 1) {
-            for (int k = 1; k <= le_occ && n < 8; k++) {
-                cand[n] = cur;
-                cand[n++].longest_edge_blocks = k * sms;
+            // triangles per lane and persistent grid
+            for (int32_t items : {2, 4}) {
+                const int occ = longest_edge_blocks_per_sm(items);
+                for (int k = 1; k <= occ && n < 16; k++) {
+                    cand[n] = cur;
+                    cand[n].longest_edge_items = items;
+                    cand[n++].longest_edge_blocks = k * sms;
+                }
             }
         } else {
             // output tile and triangles per thread (the launch configurations

@@ -73,6 +73,7 @@ struct Work {
     int32_t max_rot;
     int32_t persistent_blocks;   // grid of the sparse (tip) kernels
     int32_t le_blocks;           // grid of the persistent longest-edge kernel
+    int32_t le_items;            // longest edge: triangles per lane (2 or 4)
     // batches: the emitted he_list / v_list are made mesh-local when set
     const int32_t *loc_t_off;    // [loc_n+1] triangle offset of each mesh
     const int32_t *loc_v_off;    // [loc_n+1] vertex offset of each mesh
@@ -111,9 +112,10 @@ __host__ __device__ constexpr int64_t out_warp_count(int64_t T) { return out_rec
 constexpr int SCAN_THREADS = 1024;
 
 // longest-edge kernel: persistent warps, each with a two-stage ring of
-// 64-triangle tiles of origin bulk-copied (TMA) into shared memory
+// tiles of 32 x (2 or 4) triangles of origin bulk-copied (TMA) into shared
+// memory
 constexpr int LE_THREADS = 256;
-constexpr int LE_TILE = 64;
+constexpr int LE_ITEMS_DEFAULT = 2;
 
 // relink kernel: rl_tile triangles per CTA, rl_items per thread
 constexpr int RL_TILE_DEFAULT = 128;
@@ -194,7 +196,7 @@ __device__ __forceinline__ int32_t pv_of(int32_t e) {
 // launchers (each enqueues one kernel on stream)
 void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s);
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s);
-int longest_edge_blocks_per_sm();
+int longest_edge_blocks_per_sm(int32_t items);
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
 // allows the relink kernels their shared memory on the current device (once
 // per device before the first launch); 0 on success

@@ -122,7 +122,8 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.ctrl = reinterpret_cast<DevCtrl *>(base + OFF_CTRL);
     w.max_rot = 4096;
     w.persistent_blocks = 4 * sms;
-    w.le_blocks = longest_edge_blocks_per_sm() * sms;
+    w.le_items = LE_ITEMS_DEFAULT;
+    w.le_blocks = longest_edge_blocks_per_sm(LE_ITEMS_DEFAULT) * sms;
     w.out_tile = OUT_TILE_DEFAULT;
     w.out_items = OUT_ITEMS_DEFAULT;
     w.rl_tile = RL_TILE_DEFAULT;

@@ -78,7 +78,7 @@ class polylla_batch(ctypes.Structure):
 
 class polylla_tuning(ctypes.Structure):
     _fields_ = [("relink_tile", ctypes.c_int32), ("relink_items", ctypes.c_int32),
-                ("longest_edge_blocks", ctypes.c_int32),
+                ("longest_edge_blocks", ctypes.c_int32), ("longest_edge_items", ctypes.c_int32),
                 ("output_tile", ctypes.c_int32), ("output_items", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
