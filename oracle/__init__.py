@@ -79,6 +79,16 @@ def _bind(lib):
     lib.oracle_lepp_path.restype = ctypes.c_int32
     lib.oracle_lepp_path.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8),
                                      ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+    lib.oracle_convexify.restype = ctypes.c_int
+    lib.oracle_convexify.argtypes = [
+        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, f64p,
+        i32p, i32p, i32p, i32p,
+        u8p, i32p,
+        u8p, i32p, i32p,
+        i32p, i32p,
+        i32p, i32p, i32p, i32p,
+        i64p,
+    ]
     lib.oracle_stats_count.restype = ctypes.c_int
     assert lib.oracle_stats_count() == len(STAT_NAMES)
     return lib
@@ -218,3 +228,69 @@ def run_mesh(mesh, lib=None) -> OracleResult:
     """Convenience: run on any object with ``coords, origin, twin, next, prev,
     n_triangles`` attributes."""
     return run(mesh.coords, mesh.origin, mesh.twin, mesh.next, mesh.prev, mesh.n_triangles, lib=lib)
+
+
+@dataclass
+class ConvexResult:
+    """The convexified mesh (reading R9 of the oracle source): every
+    polygon of ``base`` split at its reflex corners by chords that are
+    existing interior edges of the triangulation."""
+
+    frontier2: np.ndarray   # [H] uint8, F1 plus both halves of every chord
+    next_out: np.ndarray    # [H] int32, the relink under F2
+    prev_out: np.ndarray    # [H] int32
+    chords: np.ndarray      # chosen half-edges, each leaving its corner's vertex
+    seeds: np.ndarray       # [P2]
+    offsets: np.ndarray     # [P2+1]
+    he_list: np.ndarray     # [N_F2]
+    v_list: np.ndarray      # [N_F2]
+    stats: dict = field(default_factory=dict)
+
+    @property
+    def n_polygons(self) -> int:
+        return int(self.seeds.shape[0])
+
+
+CONVEX_STAT_NAMES = ("polygons", "frontier", "reflex_corners", "left_reflex", "distinct_chords")
+
+
+def convexify(mesh, base: OracleResult, lib=None) -> ConvexResult:
+    """Convexify the Polylla mesh ``base`` (the result of ``run_mesh`` on
+    ``mesh``): chords at every reflex corner, relink, canonical CSR."""
+    lib = lib if lib is not None else _load()
+    coords = np.ascontiguousarray(mesh.coords, dtype=np.float64)
+    origin = np.ascontiguousarray(mesh.origin, dtype=np.int32)
+    twin = np.ascontiguousarray(mesh.twin, dtype=np.int32)
+    nxt = np.ascontiguousarray(mesh.next, dtype=np.int32)
+    prv = np.ascontiguousarray(mesh.prev, dtype=np.int32)
+    V, H, T = coords.shape[0], origin.shape[0], int(mesh.n_triangles)
+    HI = 3 * T
+    f1 = np.ascontiguousarray(base.frontier1, dtype=np.uint8)
+    n1 = np.ascontiguousarray(base.next_out, dtype=np.int32)
+    f2 = np.zeros(H, np.uint8)
+    n2 = np.zeros(H, np.int32)
+    p2 = np.zeros(H, np.int32)
+    chords = np.zeros(max(HI, 1), np.int32)
+    n_chords = np.zeros(1, np.int32)
+    seeds = np.zeros(max(T, 1), np.int32)
+    offsets = np.zeros(T + 1, np.int32)
+    he_list = np.zeros(max(HI, 1), np.int32)
+    v_list = np.zeros(max(HI, 1), np.int32)
+    stats = np.zeros(len(CONVEX_STAT_NAMES), np.int64)
+    rc = lib.oracle_convexify(
+        V, T, H, _ptr(coords, ctypes.c_double),
+        _ptr(origin, ctypes.c_int32), _ptr(twin, ctypes.c_int32), _ptr(nxt, ctypes.c_int32), _ptr(prv, ctypes.c_int32),
+        _ptr(f1, ctypes.c_uint8), _ptr(n1, ctypes.c_int32),
+        _ptr(f2, ctypes.c_uint8), _ptr(n2, ctypes.c_int32), _ptr(p2, ctypes.c_int32),
+        _ptr(chords, ctypes.c_int32), _ptr(n_chords, ctypes.c_int32),
+        _ptr(seeds, ctypes.c_int32), _ptr(offsets, ctypes.c_int32),
+        _ptr(he_list, ctypes.c_int32), _ptr(v_list, ctypes.c_int32),
+        _ptr(stats, ctypes.c_int64),
+    )
+    if rc != 0:
+        raise RuntimeError(f"oracle failed: {ERRORS.get(rc, rc)}")
+    st = {n: int(v) for n, v in zip(CONVEX_STAT_NAMES, stats)}
+    P, NF = st["polygons"], st["frontier"]
+    return ConvexResult(frontier2=f2, next_out=n2, prev_out=p2, chords=chords[: int(n_chords[0])].copy(),
+                        seeds=seeds[:P].copy(), offsets=offsets[: P + 1].copy(),
+                        he_list=he_list[:NF].copy(), v_list=v_list[:NF].copy(), stats=st)

@@ -450,3 +450,167 @@ int32_t oracle_lepp_path(int32_t T, const int32_t *twin, const uint8_t *longest,
         t = tw / 3;
     }
 }
+
+/*
+ * Convexification (post-processing).  Section 4.2 notes that keeping every
+ * half-edge of the triangulation (relinking instead of deleting) allows a
+ * later step to turn non-convex polygons into convex ones; the paper gives
+ * no method.  Reading R9, with only orientation tests:
+ *   - a corner of a polygon is a frontier half-edge e with x = next_out[e];
+ *     it sits at v = target(e).  Directions leave v: dir(h) = target(h) - v
+ *     for a half-edge h leaving v; the corner's first side is twin(e), so
+ *     dir(twin e) = origin(e) - v.
+ *   - cross(a, b) = a.x * b.y - a.y * b.x, each operation in IEEE binary64
+ *     rounded on its own.  b lies within a half turn clockwise of a iff
+ *     cross(a, b) <= 0.
+ *   - the corner is reflex iff x is not within a half turn clockwise of
+ *     twin(e): cross(dir(twin e), dir(x)) > 0.
+ *   - the candidates of a corner are the half-edges leaving v strictly
+ *     inside it, in clockwise order: y_1 = next(e) (the triangle's), then
+ *     y_{i+1} = CW(y_i), up to (not including) x -- the rotation of the
+ *     traversal, over the non-frontier half-edges it skipped.
+ *   - at a reflex corner, from cur = twin(e): take the last candidate after
+ *     cur that lies within a half turn clockwise of cur, make it a chord and
+ *     continue from it, until x lies within a half turn of cur.  (Farthest
+ *     first: the fewest chords that leave every part of the corner at most
+ *     a half turn.)
+ *   - F2 = F1 plus both halves of every chord; the polygons are the
+ *     traversal (reading R5) under F2, listed as in reading R8.
+ * Corners are processed independently from F1 and next_out, so the result
+ * does not depend on their order.  A corner left reflex because its
+ * candidates ran out (not possible when every triangle has positive area)
+ * is counted in stats[3].
+ *
+ * In:  the mesh's input arrays; frontier1 [H] and next_out [H] of
+ *      oracle_polylla.
+ * Out: frontier2 [H]; next2, prev2 [H]; chords [3T] (the chosen half-edges,
+ *      each leaving its corner's vertex; *n_chords of them); the CSR seeds
+ *      [T], offsets [T+1], he_list, v_list [3T]; stats[0] polygons,
+ *      stats[1] F2 frontier interior half-edges, stats[2] reflex corners,
+ *      stats[3] corners left reflex, stats[4] distinct chord edges.
+ */
+static void half_dir(const mesh_t *m, int32_t h, int32_t v, double *dx, double *dy) {
+    /* direction of the half-edge h leaving v: target(h) - v */
+    const int32_t t = q_target(m, h);
+    *dx = m->xy[2 * (int64_t)t] - m->xy[2 * (int64_t)v];
+    *dy = m->xy[2 * (int64_t)t + 1] - m->xy[2 * (int64_t)v + 1];
+}
+
+static double cross2(double ax, double ay, double bx, double by) {
+    const double p = ax * by;
+    const double q = ay * bx;
+    return p - q;
+}
+
+int oracle_convexify(int32_t V, int32_t T, int32_t H, const double *coords,
+                     const int32_t *origin, const int32_t *twin, const int32_t *next, const int32_t *prev,
+                     const uint8_t *frontier1, const int32_t *next_out,
+                     uint8_t *frontier2, int32_t *next2, int32_t *prev2,
+                     int32_t *chords, int32_t *n_chords,
+                     int32_t *seeds, int32_t *offsets, int32_t *he_list, int32_t *v_list,
+                     int64_t *stats) {
+    mesh_t mesh = {V, T, H, coords, origin, twin, next, prev};
+    const mesh_t *m = &mesh;
+    const int32_t HI = 3 * T;
+    int status = OR_OK;
+    int64_t n_reflex = 0, n_left = 0;
+    int32_t nc = 0;
+    uint8_t *visited = (uint8_t *)calloc((size_t)H, 1);
+    int32_t *fan = (int32_t *)malloc(sizeof(int32_t) * (size_t)(H + 1));
+    if (!visited || !fan) { status = OR_ERR_ALLOC; goto done; }
+    memcpy(frontier2, frontier1, (size_t)H);
+
+    /* ---- chords at reflex corners ---- */
+    for (int32_t e = 0; e < HI; e++) {
+        if (!frontier1[e]) continue;
+        const int32_t x = next_out[e];
+        const int32_t v = q_target(m, e);
+        double ux, uy, wx, wy;
+        half_dir(m, twin[e], v, &ux, &uy);
+        half_dir(m, x, v, &wx, &wy);
+        if (!(cross2(ux, uy, wx, wy) > 0.0)) continue;
+        n_reflex++;
+        /* the candidates, clockwise from the triangle's next half-edge */
+        int32_t n_fan = 0, y = next[e];
+        while (y != x) {
+            if (n_fan > H) { status = OR_ERR_NONTERMINATING; goto done; }
+            fan[n_fan++] = y;
+            y = q_cw(m, y);
+        }
+        int32_t i = 0;                       /* next candidate after cur */
+        while (cross2(ux, uy, wx, wy) > 0.0) {
+            int32_t best = -1;
+            while (i < n_fan) {
+                double dx, dy;
+                half_dir(m, fan[i], v, &dx, &dy);
+                if (cross2(ux, uy, dx, dy) <= 0.0) {
+                    best = i;
+                    i++;
+                } else {
+                    break;
+                }
+            }
+            if (best < 0) {                  /* no candidate within a half turn */
+                n_left++;
+                break;
+            }
+            const int32_t c = fan[best];
+            frontier2[c] = 1;
+            frontier2[twin[c]] = 1;
+            chords[nc++] = c;
+            half_dir(m, c, v, &ux, &uy);
+        }
+    }
+    *n_chords = nc;
+
+    /* ---- relink under F2 (reading R5), every frontier half-edge ---- */
+    memcpy(next2, next, sizeof(int32_t) * (size_t)H);
+    memcpy(prev2, prev, sizeof(int32_t) * (size_t)H);
+    for (int32_t e = 0; e < HI; e++) {
+        if (!frontier2[e] || visited[e]) continue;
+        const int64_t len = traverse(m, frontier2, e, next2, prev2, visited, NULL, NULL, NULL);
+        if (len < 0) { status = (int)len; goto done; }
+    }
+
+    /* ---- output (reading R8) ---- */
+    memset(visited, 0, (size_t)H);
+    int64_t n_poly = 0, k = 0;
+    for (int32_t e = 0; e < HI; e++) {
+        if (!frontier2[e] || visited[e]) continue;
+        seeds[n_poly] = e;
+        offsets[n_poly] = (int32_t)k;
+        int32_t cur = e;
+        do {
+            if (cur < 0 || cur >= HI || !frontier2[cur] || visited[cur]) {
+                status = OR_ERR_NOT_A_CYCLE;
+                goto done;
+            }
+            visited[cur] = 1;
+            he_list[k] = cur;
+            v_list[k] = origin[cur];
+            k++;
+            cur = next2[cur];
+        } while (cur != e);
+        n_poly++;
+    }
+    offsets[n_poly] = (int32_t)k;
+    {
+        /* distinct chord edges */
+        int64_t distinct = 0;
+        memset(visited, 0, (size_t)H);
+        for (int32_t j = 0; j < nc; j++) {
+            const int32_t id = edge_id(m, chords[j]);
+            if (!visited[id]) { visited[id] = 1; distinct++; }
+        }
+        stats[4] = distinct;
+    }
+    stats[0] = n_poly;
+    stats[1] = k;
+    stats[2] = n_reflex;
+    stats[3] = n_left;
+
+done:
+    free(visited);
+    free(fan);
+    return status;
+}

@@ -6,8 +6,10 @@ of ``test_oracle_pins`` fails on it.  The mistakes are the kind a reader of
 the paper could make: a dropped term, a reversed rotation, an off-by-one
 rotation count, the frontier condition as printed in Algorithm 3, a wrong
 tie-break, a missing seed rule, output not started at the polygon minimum,
-and, for the Lepp, the wrong half of a terminal edge or a path that stops
-before the terminal edge's second triangle.
+for the Lepp, the wrong half of a terminal edge or a path that stops
+before the terminal edge's second triangle, and, for the convexification,
+a flipped turn test, swapped cross-product operands, the nearest instead
+of the farthest chord, and a chord with only one half on the frontier.
 """
 import os
 import shutil
@@ -17,6 +19,7 @@ import pytest
 
 import oracle
 from paper_2403_14723_gb300 import meshgen
+from tests import test_oracle_convex as convex_pins
 from tests import test_oracle_lepp as lepp_pins
 from tests import test_oracle_pins as pins
 
@@ -46,6 +49,15 @@ MUTANTS = {
                          "                terminal[t0] = tw;\n                break;"),
     "lepp_path_stops_before_terminal": ("        path[n++] = tw / 3;\n        if (longest[tw]) return n;",
                                         "        if (longest[tw]) return n;\n        path[n++] = tw / 3;"),
+    # convexification (reading R9)
+    "convex_reflex_sign_flipped": ("        if (!(cross2(ux, uy, wx, wy) > 0.0)) continue;",
+                                   "        if (!(cross2(ux, uy, wx, wy) < 0.0)) continue;"),
+    "convex_nearest_candidate": ("                    best = i;\n                    i++;\n                } else {",
+                                 "                    best = i;\n                    i++;\n                    break;\n"
+                                 "                } else {"),
+    "convex_one_chord_half": ("            frontier2[twin[c]] = 1;\n", ""),
+    "convex_cross_operands_swapped": ("    const double p = ax * by;\n    const double q = ay * bx;",
+                                      "    const double p = ay * bx;\n    const double q = ax * by;"),
 }
 
 
@@ -76,6 +88,9 @@ def _pins_hold(lib) -> bool:
         lambda: lepp_pins.pin_lepp_terminal(meshgen.random_delaunay(130, seed=301), lib),
         lambda: lepp_pins.pin_lepp_recursion(meshgen.random_delaunay(200, seed=302), lib),
         lambda: lepp_pins.pin_lepp_grid(5, lib),
+        lambda: convex_pins.pin_convex(meshgen.random_delaunay(300, seed=401), lib),
+        lambda: convex_pins.pin_convex(meshgen.perturbed_grid(24, 0.3, seed=401), lib),
+        lambda: convex_pins.pin_fixed_point(meshgen.random_delaunay(500, seed=430), lib),
     ]
     for c in cases:
         try:
