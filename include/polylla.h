@@ -312,6 +312,38 @@ int polylla_autotune(polylla_ctx *ctx, int32_t reps, polylla_tuning *out, polyll
 int polylla_tuning_cache_clear(void);
 
 /*
+ * Convexification (post-processing; Section 4.2 keeps every half-edge of
+ * the triangulation, relinking instead of deleting, so that a later step
+ * can turn non-convex polygons into convex ones -- the paper gives no
+ * method, so this is the library's own rule).  polylla_convexify runs on the
+ * context's last generate (same stream, after it) and splits every reflex
+ * corner of every polygon with the fewest edges of the triangulation
+ * itself:
+ *   - the corner at a frontier half-edge e is (e, x = next(e)) at
+ *     v = target(e); with directions leaving v (dir(h) = target(h) - v,
+ *     the corner's first side twin(e), dir = origin(e) - v) and
+ *     cross(a, b) = a.x b.y - a.y b.x in binary64 (each operation rounded
+ *     to nearest, no FMA), the corner is reflex iff cross(dir twin e,
+ *     dir x) > 0;
+ *   - from cur = twin(e), the last of the corner's interior half-edges
+ *     (clockwise from the triangle's next of e, the relink's rotation)
+ *     within a half turn clockwise of cur (cross <= 0) becomes a chord and
+ *     the new cur, until x lies within a half turn of cur.
+ * Both halves of every chord join the frontier (flags bits 0-2 of
+ * polylla_get_labels then hold this frontier), next/prev around the chord
+ * ends are relinked as by the repair, and polylla_get_polygons returns the
+ * convex polygons (same canonical order).  Every corner of the result
+ * turns by at most a half turn.  The first call allocates the chord list
+ * (4 x 3T bytes); later calls allocate nothing.  Single-mesh contexts only
+ * (INVALID_ARGUMENT on a batch).  Asynchronous; device errors through
+ * polylla_last_error.  polylla_convex_chords gives the chosen half-edges of
+ * the last convexify (device pointer owned by the context, *n of them, each
+ * leaving its corner's vertex; one host synchronization).
+ */
+int polylla_convexify(polylla_ctx *ctx, polylla_stream stream);
+int polylla_convex_chords(polylla_ctx *ctx, const int32_t **chords, int32_t *n, polylla_stream stream);
+
+/*
  * Longest-edge propagation paths (Definition 1, Section 3.1; Section 1
  * lists a data-parallel Lepp among the paper's contributions, as a building
  * block for Lepp-based refinement).  Lepp(t0) = t0, t1, ...: t_i is the

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["polylla_api.cu", "kernels_label.cu", "kernels_repair.cu", "kernels_output.cu", "kernels_batch.cu",
-           "kernels_serve.cu", "polylla_noalloc.cu", "polylla_server.cu", "kernels_lepp.cu"]
+           "kernels_serve.cu", "polylla_noalloc.cu", "polylla_server.cu", "kernels_lepp.cu", "kernels_convex.cu"]
 HEADERS = [os.path.join(CSRC, "polylla_internal.cuh"), os.path.join(CSRC, "polylla_serve.cuh"),
            os.path.join(CSRC, "serve_policy.h"), os.path.join(INCLUDE, "polylla.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

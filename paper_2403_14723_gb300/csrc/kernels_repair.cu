@@ -103,12 +103,15 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
     set_start(w.flags, c);
 }
 
-__global__ void __launch_bounds__(256) k_chord_links(MeshView m, Work w) {
+// over a list of chords (*count of them, at most cap; negative entries are
+// skipped): the repair's chords, or the convexification's
+__global__ void __launch_bounds__(256) k_chord_links(MeshView m, Work w, const int32_t *list, const int32_t *count,
+                                                     int32_t cap) {
     const int32_t HI = 3 * m.T;
-    int32_t n = w.ctrl->n_tips;
-    if (n > w.tip_cap) n = w.tip_cap;
+    int32_t n = *count;
+    if (n > cap) n = cap;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n; i += gridDim.x * blockDim.x) {
-        const int32_t c0 = w.chords[i >> 1];
+        const int32_t c0 = list[i >> 1];
         if (c0 < 0) continue;
         const int32_t c = (i & 1) ? __ldg(m.twin + c0) : c0;
         relink_around(m, w, c, HI);
@@ -116,7 +119,12 @@ __global__ void __launch_bounds__(256) k_chord_links(MeshView m, Work w) {
 }
 
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s) {
-    k_chord_links<<<w.persistent_blocks, 256, 0, s>>>(m, w);
+    k_chord_links<<<w.persistent_blocks, 256, 0, s>>>(m, w, w.chords, &w.ctrl->n_tips, w.tip_cap);
+}
+
+void launch_chord_links_list(const MeshView &m, const Work &w, const int32_t *list, const int32_t *count,
+                             int32_t cap, cudaStream_t s) {
+    k_chord_links<<<w.persistent_blocks, 256, 0, s>>>(m, w, list, count, cap);
 }
 
 }  // namespace polylla

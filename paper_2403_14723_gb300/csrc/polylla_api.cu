@@ -58,6 +58,10 @@ struct polylla_ctx {
     cudaEvent_t ev_twin = nullptr, ev_links = nullptr;
     cudaEvent_t wait_before_relink = nullptr;  // enqueue: stage 1 waits for it
     cudaEvent_t record_after_links = nullptr;  // enqueue: recorded after stage 3
+    // convexification: its chord list (allocated by the first call) and count
+    int32_t *cv_list = nullptr;
+    int32_t *cv_count = nullptr;
+    int32_t cv_cap = 0;
     // captured generate (polylla_capture_graph)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -824,6 +828,47 @@ int polylla_tuning_cache_clear(void) {
 }
 
 // ---- Lepp ------------------------------------------------------------------------
+
+int polylla_convexify(polylla_ctx *c, polylla_stream stream) {
+    if (!c || c->is_batch) return POLYLLA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->cv_list) {
+        // every chord is a distinct non-frontier interior half-edge: 3T bound
+        void *p = nullptr;
+        int rc = dev_alloc(c, &p, sizeof(int32_t) * 3 * (size_t)c->mesh.T);
+        if (rc) return rc;
+        c->cv_list = (int32_t *)p;
+        if ((rc = dev_alloc(c, &p, sizeof(int32_t)))) return rc;
+        c->cv_count = (int32_t *)p;
+        c->cv_cap = 3 * c->mesh.T;
+    }
+    c->last_stream = s;
+    const int32_t tile = polygons_config_valid(c->w.out_tile, c->w.out_items) ? c->w.out_tile : OUT_TILE_DEFAULT;
+    const size_t n_tiles = ((size_t)c->mesh.T + tile - 1) / tile;
+    CK(cudaMemsetAsync(c->cv_count, 0, sizeof(int32_t), s));
+    CK(cudaMemsetAsync(c->w.tile_state, 0, sizeof(unsigned long long) * n_tiles, s));
+    launch_convex_chords(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
+    launch_convex_mark(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
+    launch_chord_links_list(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
+    launch_poly_count(c->mesh, c->w, s);
+    launch_tile_scan(c->mesh, c->w, s);
+    launch_poly_list(c->mesh, c->w, s);
+    CK(cudaGetLastError());
+    return POLYLLA_OK;
+}
+
+int polylla_convex_chords(polylla_ctx *c, const int32_t **chords, int32_t *n, polylla_stream stream) {
+    if (!c || !chords || !n || c->is_batch) return POLYLLA_ERR_INVALID_ARGUMENT;
+    *chords = c->cv_list;
+    *n = 0;
+    if (!c->cv_list) return POLYLLA_OK;
+    int32_t h = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(&h, c->cv_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n = h < c->cv_cap ? h : c->cv_cap;
+    return POLYLLA_OK;
+}
 
 int polylla_lepp_terminal(polylla_ctx *c, int32_t *terminal, int32_t *length, polylla_stream stream) {
     if (!c || !terminal || c->is_batch || c->serve) return POLYLLA_ERR_INVALID_ARGUMENT;

@@ -204,6 +204,13 @@ int relink_configure();
 bool relink_config_valid(int32_t tile, int32_t items);
 void launch_chords(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
+void launch_chord_links_list(const MeshView &m, const Work &w, const int32_t *list, const int32_t *count,
+                             int32_t cap, cudaStream_t s);
+// convexification (kernels_convex.cu)
+void launch_convex_chords(const MeshView &m, const Work &w, int32_t *list, int32_t *count, int32_t cap,
+                          cudaStream_t s);
+void launch_convex_mark(const MeshView &m, const Work &w, const int32_t *list, const int32_t *count, int32_t cap,
+                        cudaStream_t s);
 void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_poly_list(const MeshView &m, const Work &w, cudaStream_t s);

@@ -159,6 +159,9 @@ _SIGNATURES = {
                                         ctypes.c_void_p]),
     "polylla_tuning_cache_clear": (ctypes.c_int, []),
     "polylla_lepp_terminal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polylla_convexify": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polylla_convex_chords": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "polylla_lepp_paths": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "polylla_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(polylla_server_options)]),
@@ -508,6 +511,26 @@ def polylla_batch_polygon_offsets(ctx: int, n_meshes: int):
     return _view(p.value, n_meshes + 1, "<i4", torch.int32)
 
 
+def polylla_convexify(ctx: int, stream=None) -> None:
+    """Split every reflex corner of the last generate's polygons with the
+    fewest triangulation edges (see include/polylla.h); the convex polygons
+    then come from polylla_get_polygons."""
+    _check(load_library().polylla_convexify(ctypes.c_void_p(ctx), _stream_ptr(stream)), "polylla_convexify")
+
+
+def polylla_convex_chords(ctx: int, stream=None):
+    """The half-edges the last convexify chose (device int32 tensor)."""
+    import torch
+
+    p = ctypes.c_void_p()
+    n = ctypes.c_int32()
+    _check(load_library().polylla_convex_chords(ctypes.c_void_p(ctx), ctypes.byref(p), ctypes.byref(n),
+                                                _stream_ptr(stream)), "polylla_convex_chords")
+    if n.value == 0:
+        return torch.empty(0, dtype=torch.int32, device="cuda")
+    return _view(p.value, n.value, "<i4", torch.int32)
+
+
 def polylla_lepp_terminal(ctx: int, n_triangles: int, with_length: bool = True, stream=None):
     """Lepp terminal seed (and path length) of every triangle, after a
     generate: device int32 tensors ``(terminal, length or None)``."""
@@ -663,6 +686,9 @@ class Polylla:
 
     def labels(self, stream=None) -> dict:
         return polylla_get_labels(self.ctx, self.mesh.n_triangles, stream)
+
+    def convexify(self, stream=None) -> None:
+        polylla_convexify(self.ctx, stream)
 
     def close(self):
         polylla_destroy(self.ctx)
