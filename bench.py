@@ -452,6 +452,27 @@ def run_gb300(args):
             "api": "polylla_lepp_terminal: terminal seed and path length of every triangle"}
     del term_buf, len_buf
 
+    # ---- convexification of the same mesh (post-processing) --------------
+    cv_steps = max(3, min(args.steps, 20))
+    cs = [torch.cuda.Event(enable_timing=True) for _ in range(cv_steps)]
+    ce = [torch.cuda.Event(enable_timing=True) for _ in range(cv_steps)]
+    for i in range(cv_steps + 1):
+        polylla.polylla_generate(ctx, stream)
+        flush.fill_(i)
+        if i > 0:
+            cs[i - 1].record(stream)
+        polylla.polylla_convexify(ctx, stream)
+        if i > 0:
+            ce[i - 1].record(stream)
+    torch.cuda.synchronize()
+    cv_out = polylla.polylla_get_polygons(ctx, stream)
+    cv_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(cs, ce))
+    convex = {"ms": cv_ms, "triangles_per_s": T / (cv_ms * 1e-3), "polygons_before": P,
+              "polygons_after": cv_out["n_polygons"], "chords": cv_out["n_polygons"] - P,
+              "frontier_halfedges_after": cv_out["n_frontier"],
+              "api": "polylla_convexify after a generate: chords at reflex corners, relink, CSR again"}
+    polylla.polylla_generate(ctx, stream)
+
     # ---- end to end through the host-buffer entry point ------------------
     e2e = None
     if not args.no_e2e:
@@ -579,7 +600,7 @@ def run_gb300(args):
                        "l2": f"256 MiB buffer written between timed steps (L2 flush); inputs "
                              f"{(16 * V + 16 * H) / 1e9:.2f} GB"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "lepp": lepp,
-            "batched": batched, "served": served,
+            "batched": batched, "served": served, "convexify": convex,
             "gpu_launches": launches, "clocks": clocks,
             "kernel_digest": kernel_digest(), "core_kernel_digest": core_kernel_digest(),
         }
