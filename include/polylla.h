@@ -286,9 +286,10 @@ int polylla_release_graph(polylla_ctx *ctx);
  * threads labels and links: (64, 1), (128, 1), (256, 1), (256, 2) or
  * (256, 4); longest_edge_items the triangles per lane of the persistent
  * longest-edge kernel (2 or 4) and longest_edge_blocks its grid (blocks,
- * in [1, 64 * SMs]); output_tile the triangles per tile of the output kernel (1024, 2048 or
- * 4096) and output_items the triangles each of its threads walks and lists
- * (4 or 8; a tile of 4096 with 4 per thread is a block of 1024 threads).
+ * in [1, 64 * SMs]); output_tile the triangles per tile of the output
+ * kernels and output_items the triangles each of their threads walks and
+ * lists: (1024, 2), (1024, 4), (2048, 2), (2048, 4) or (4096, 4) (blocks
+ * of tile / items threads).
  * polylla_autotune times whole generates (reps per setting, median of the
  * stage's CUDA-event time), tries the candidates of one setting at a time in
  * stage order and keeps the fastest, applies the result to the context,

@@ -18,7 +18,7 @@
 //   k_poly_count  walks the starts of its tile (leaving the tile only for
 //                 the polygons that cross it) and totals the minima's
 //                 (count, length) pairs per warp and per tile;
-//   k_tile_scan   scans the tile totals (one block);
+//   k_tile_scan   scans the tile totals per group of 1024 tiles;
 //   k_poly_list   lists every warp's polygons through a staging buffer
 //                 that goes out with coalesced stores.
 // No warp waits for another warp.  Two designs that did were slower: a
@@ -95,6 +95,17 @@ void launch_scan_u64(const unsigned long long *in, unsigned long long *out, int3
     k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(in, out, n, grand);
 }
 
+// ---- per-thread records of the count pass ------------------------------------
+// One 64-bit word per thread: bits 0-30 the length of the warp's minima
+// before the thread (< 2^31 since N_F <= 3T < 2^31), bits 31-40 their count
+// (< 32 x 3 x 8), bits 41-63 the mask of the thread's own minima (3 bits per
+// triangle, at most 7 triangles per thread).
+constexpr int REC_CNT_SHIFT = 31;
+constexpr int REC_MASK_SHIFT = 41;
+constexpr int REC_MASK_BITS = 64 - REC_MASK_SHIFT;
+constexpr unsigned long long REC_LEN_MASK = (1ull << REC_CNT_SHIFT) - 1ull;
+constexpr unsigned long long REC_CNT_MASK = (1ull << (REC_MASK_SHIFT - REC_CNT_SHIFT)) - 1ull;
+
 // ---- tiles -----------------------------------------------------------------
 // A tile is TILE consecutive triangles (3 TILE half-edges); its copies start
 // on 16-byte boundaries (TILE is a multiple of 16) and round their length up
@@ -119,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_poly_count(MeshView m, Work w) {
     constexpr int IPT = TILE / NT;
     constexpr int E = 3 * TILE;
     constexpr int NW = NT / 32;
-    static_assert(TILE % NT == 0 && IPT >= 1 && 3 * IPT <= 32, "a thread's half-edges fit one 32-bit mask");
+    static_assert(TILE % NT == 0 && IPT >= 1 && 3 * IPT <= REC_MASK_BITS, "a thread's minima fit its record");
     static_assert(TILE % 16 == 0, "tile copies start on 16-byte boundaries");
     extern __shared__ __align__(128) unsigned char smem[];
     int32_t *s_nx = reinterpret_cast<int32_t *>(smem);         // [E]
@@ -183,8 +194,9 @@ __global__ void __launch_bounds__(NT) k_poly_count(MeshView m, Work w) {
     }
     const unsigned long long v = ((unsigned long long)cnt << 32) | len;
     const unsigned long long inc = warp_incl_scan(v, lane);
-    w.poly_rec[rec] = inc - v;
-    w.poly_min[rec] = minmask;
+    const unsigned long long ex = inc - v;  // (minima, length) of the lanes before, in the warp
+    w.poly_rec[rec] = (ex & REC_LEN_MASK) | ((ex >> 32) << REC_CNT_SHIFT) |
+                      ((unsigned long long)minmask << REC_MASK_SHIFT);
     if (lane == 31) {
         w.poly_wtot[(int64_t)tile * NW + wid] = inc;
         atomicAdd(w.tile_state + tile, inc);
@@ -194,20 +206,37 @@ __global__ void __launch_bounds__(NT) k_poly_count(MeshView m, Work w) {
 }
 
 // ===========================================================================
-// k_tile_scan: one block, exclusive scan of the tiles' (polygons, length)
-// totals into tile_pre; thread 0 then writes P, N_F and offsets[P] and
-// checks the capacities.
+// k_tile_scan: one block per group of SCAN_THREADS tiles: the exclusive scan
+// of the tiles' (polygons, length) totals within the group (tile_pre) and
+// the group's total (group_tot).  The last block to finish (a counter in
+// the control block) scans the group totals into group_pre and ends the
+// output: P, N_F and offsets[P].  A tile's place in the output is then
+// tile_pre[tile] + group_pre[its group], and no block waits for another.
 // ===========================================================================
 __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(MeshView m, Work w, int32_t n) {
     __shared__ unsigned long long s_warp[33];
+    __shared__ int s_last;
+    const int32_t i = blockIdx.x * SCAN_THREADS + threadIdx.x;
+    const unsigned long long v = i < n ? w.tile_state[i] : 0ull;
+    unsigned long long total;
+    const unsigned long long ex = block_excl_scan(v, s_warp, &total);
+    if (i < n) w.tile_pre[i] = ex;
+    if (threadIdx.x == 0) {
+        w.group_tot[blockIdx.x] = total;
+        __threadfence();  // the total is visible before the count says so
+        s_last = atomicAdd(&w.ctrl->scan_done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     unsigned long long carry = 0;
-    for (int32_t b = 0; b < n; b += SCAN_THREADS) {
-        const int32_t i = b + threadIdx.x;
-        const unsigned long long v = i < n ? w.tile_state[i] : 0ull;
-        unsigned long long total;
-        const unsigned long long ex = block_excl_scan(v, s_warp, &total);
-        if (i < n) w.tile_pre[i] = carry + ex;
-        carry += total;
+    for (int32_t b = 0; b < (int32_t)gridDim.x; b += SCAN_THREADS) {
+        const int32_t g = b + threadIdx.x;
+        const unsigned long long x = g < (int32_t)gridDim.x ? __ldcg(w.group_tot + g) : 0ull;
+        unsigned long long t;
+        const unsigned long long e = block_excl_scan(x, s_warp, &t);
+        if (g < (int32_t)gridDim.x) w.group_pre[g] = carry + e;
+        carry += t;
     }
     if (threadIdx.x != 0) return;
     int64_t P = (int64_t)(carry >> 32);
@@ -261,14 +290,16 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     }
     __syncthreads();
     const int64_t rec = (int64_t)tile * NT + threadIdx.x;
-    const unsigned long long ex = w.poly_rec[rec];
-    uint32_t minmask = w.poly_min[rec];
+    const unsigned long long r = w.poly_rec[rec];
+    const unsigned long long ex = ((r >> REC_CNT_SHIFT) & REC_CNT_MASK) << 32 | (r & REC_LEN_MASK);
+    uint32_t minmask = (uint32_t)(r >> REC_MASK_SHIFT);
     // the warps before this one in the tile, and this warp's own total
     const unsigned long long wt = lane <= wid ? w.poly_wtot[(int64_t)tile * NW + lane] : 0ull;
     const unsigned long long wbase = warp_sum(lane < wid ? wt : 0ull);
     const unsigned long long wtot = __shfl_sync(0xffffffffu, wt, wid);
-    // the tiles before this one
-    const unsigned long long tbase = w.tile_pre[tile];
+    // the tiles before this one: those of the groups before its group, then
+    // those before it in its group
+    const unsigned long long tbase = w.group_pre[tile / SCAN_THREADS] + w.tile_pre[tile];
     if (!__all_sync(0xffffffffu, mbar_wait(&s_bar, 0))) {
         if (lane == 0) {
             atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
@@ -344,11 +375,10 @@ constexpr size_t list_smem() {
 
 #define POLYGON_CONFIGS(X) \
     X(1024, 256)           \
-    X(1024, 128)           \
+    X(1024, 512)           \
     X(2048, 512)           \
-    X(2048, 256)           \
-    X(4096, 1024)          \
-    X(4096, 512)
+    X(2048, 1024)          \
+    X(4096, 1024)
 
 bool polygons_config_valid(int32_t tile, int32_t items) {
 #define X(TL, N) \
@@ -399,7 +429,8 @@ void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s) {
 
 void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s) {
     const int32_t tile = polygons_config_valid(w.out_tile, w.out_items) ? w.out_tile : 2048;
-    k_tile_scan<<<1, SCAN_THREADS, 0, s>>>(m, w, (m.T + tile - 1) / tile);
+    const int32_t n = (m.T + tile - 1) / tile;
+    k_tile_scan<<<(n + SCAN_THREADS - 1) / SCAN_THREADS, SCAN_THREADS, 0, s>>>(m, w, n);
 }
 
 void launch_poly_list(const MeshView &m, const Work &w, cudaStream_t s) {

@@ -216,10 +216,12 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.tile_state = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)c->w.n_tile_max))) return rc;
     c->w.tile_pre = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)(c->w.n_tile_max / SCAN_THREADS + 1)))) return rc;
+    c->w.group_tot = (unsigned long long *)p;
+    if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)(c->w.n_tile_max / SCAN_THREADS + 1)))) return rc;
+    c->w.group_pre = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)out_rec_count(T)))) return rc;
     c->w.poly_rec = (unsigned long long *)p;
-    if ((rc = dev_alloc(c, &p, sizeof(uint32_t) * (size_t)out_rec_count(T)))) return rc;
-    c->w.poly_min = (uint32_t *)p;
     if ((rc = dev_alloc(c, &p, sizeof(unsigned long long) * (size_t)out_warp_count(T)))) return rc;
     c->w.poly_wtot = (unsigned long long *)p;
     if ((rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)T))) return rc;
@@ -786,7 +788,7 @@ int polylla_autotune(polylla_ctx *c, int32_t reps, polylla_tuning *out, polylla_
         } else {
             // output tile and triangles per thread (the launch configurations
             // the library is built with)
-            const int32_t pairs[][2] = {{1024, 4}, {1024, 8}, {2048, 4}, {2048, 8}, {4096, 4}, {4096, 8}};
+            const int32_t pairs[][2] = {{1024, 2}, {1024, 4}, {2048, 2}, {2048, 4}, {4096, 4}};
             for (const auto &pr : pairs)
                 if (polygons_config_valid(pr[0], pr[1]) && polygons_blocks_per_sm(pr[0], pr[1]) > 0) {
                     cand[n] = cur;
@@ -847,6 +849,7 @@ int polylla_convexify(polylla_ctx *c, polylla_stream stream) {
     const size_t n_tiles = ((size_t)c->mesh.T + tile - 1) / tile;
     CK(cudaMemsetAsync(c->cv_count, 0, sizeof(int32_t), s));
     CK(cudaMemsetAsync(c->w.tile_state, 0, sizeof(unsigned long long) * n_tiles, s));
+    CK(cudaMemsetAsync(&c->w.ctrl->scan_done, 0, sizeof(int32_t), s));
     launch_convex_chords(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
     launch_convex_mark(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
     launch_chord_links_list(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);

@@ -9,9 +9,11 @@
 //   tips    [V]   int32  F0 half-edge leaving each barrier tip
 //   chords  [V]   int32  chord half-edge leaving each barrier tip
 //   tile_state, tile_pre [T/1024] u64  (polygons, length) total of each output
-//                        tile, and their exclusive scan
-//   poly_rec [T/4+1025] u64, poly_min [..] u32   per output thread: its
-//                        (polygons, length) offset in its warp's range, its minima
+//                        tile, and their exclusive scan within groups of
+//                        1024 tiles; group_tot, group_pre [T/2^20 + 1] u64 the
+//                        groups' totals and their exclusive scan
+//   poly_rec [T/2+2049] u64  per output thread: its (polygons, length)
+//                        offset in its warp's range and the mask of its minima
 //   poly_wtot [T/128+34] u64  per output warp: its (polygons, length) total
 //   seeds [T], offsets [T+1], he_list [3T], v_list [3T]   CSR output
 //   ctrl          DevCtrl       counters and the device error word
@@ -37,7 +39,8 @@ struct DevCtrl {
     int32_t n_tips;       // barrier tips found by the relink
     int32_t n_polygons;   // P
     int32_t n_frontier;   // N_F
-    int32_t pad[4];
+    int32_t scan_done;    // tile-scan blocks finished
+    int32_t pad[3];
 };
 
 struct MeshView {
@@ -56,9 +59,10 @@ struct Work {
     int32_t *chords;
     int32_t tip_cap;
     unsigned long long *tile_state; // (polygons, length) total per output tile [n_tile_max]
-    unsigned long long *tile_pre;   // their exclusive scan [n_tile_max]
-    unsigned long long *poly_rec;   // per output thread: place in its tile [n_rec_max]
-    uint32_t *poly_min;             // per output thread: mask of its minima [n_rec_max]
+    unsigned long long *tile_pre;   // their exclusive scan within groups of SCAN_THREADS tiles
+    unsigned long long *group_tot;  // each group's total [n_tile_max / SCAN_THREADS + 1]
+    unsigned long long *group_pre;  // their exclusive scan [n_tile_max / SCAN_THREADS + 1]
+    unsigned long long *poly_rec;   // per output thread: its place in its warp and its minima [n_rec_max]
     unsigned long long *poly_wtot;  // per output warp: (polygons, length) of its range
     int32_t n_tile_max;             // ceil(T / OUT_TILE_MIN)
     int32_t out_tile;               // output tile: triangles
@@ -103,7 +107,7 @@ struct BatchView {
 // per thread; single-block scans (Lepp paths) with SCAN_THREADS threads
 constexpr int OUT_TILE_MIN = 1024;
 constexpr int OUT_TILE_MAX = 4096;
-constexpr int OUT_ITEMS_MIN = 4;
+constexpr int OUT_ITEMS_MIN = 2;
 constexpr int OUT_TILE_DEFAULT = 2048;
 constexpr int OUT_ITEMS_DEFAULT = 4;
 // per-thread records of the output stage for T triangles, any configuration

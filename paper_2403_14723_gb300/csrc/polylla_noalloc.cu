@@ -32,9 +32,10 @@ constexpr size_t OFF_TIPS = OFF_FLAGS + up256(NA_MAX_T);
 constexpr size_t OFF_CHORDS = OFF_TIPS + up256(4 * (size_t)NA_MAX_V);
 constexpr size_t OFF_TILES = OFF_CHORDS + up256(4 * (size_t)NA_MAX_V);
 constexpr size_t OFF_TILE_PRE = OFF_TILES + up256(8 * (size_t)NA_MAX_TILES);
-constexpr size_t OFF_REC = OFF_TILE_PRE + up256(8 * (size_t)NA_MAX_TILES);
-constexpr size_t OFF_MIN = OFF_REC + up256(8 * (size_t)out_rec_count(NA_MAX_T));
-constexpr size_t OFF_WTOT = OFF_MIN + up256(4 * (size_t)out_rec_count(NA_MAX_T));
+constexpr size_t OFF_GROUPS = OFF_TILE_PRE + up256(8 * (size_t)NA_MAX_TILES);
+constexpr size_t OFF_GROUP_PRE = OFF_GROUPS + up256(8 * (size_t)(NA_MAX_TILES / SCAN_THREADS + 1));
+constexpr size_t OFF_REC = OFF_GROUP_PRE + up256(8 * (size_t)(NA_MAX_TILES / SCAN_THREADS + 1));
+constexpr size_t OFF_WTOT = OFF_REC + up256(8 * (size_t)out_rec_count(NA_MAX_T));
 constexpr size_t OFF_CTRL = OFF_WTOT + up256(8 * (size_t)out_warp_count(NA_MAX_T));
 constexpr size_t NA_BYTES = OFF_CTRL + up256(sizeof(DevCtrl));
 
@@ -111,8 +112,9 @@ extern "C" int polylla_generate_noalloc(const polylla_mesh *mesh, int32_t *seeds
     w.tip_cap = V;
     w.tile_state = reinterpret_cast<unsigned long long *>(base + OFF_TILES);
     w.tile_pre = reinterpret_cast<unsigned long long *>(base + OFF_TILE_PRE);
+    w.group_tot = reinterpret_cast<unsigned long long *>(base + OFF_GROUPS);
+    w.group_pre = reinterpret_cast<unsigned long long *>(base + OFF_GROUP_PRE);
     w.poly_rec = reinterpret_cast<unsigned long long *>(base + OFF_REC);
-    w.poly_min = reinterpret_cast<uint32_t *>(base + OFF_MIN);
     w.poly_wtot = reinterpret_cast<unsigned long long *>(base + OFF_WTOT);
     w.n_tile_max = (int32_t)(((int64_t)T + OUT_TILE_MIN - 1) / OUT_TILE_MIN);
     w.seeds = seeds;

@@ -96,7 +96,7 @@ int64_t slot_bytes(int64_t n, int64_t V, int64_t T, int64_t H) {
     const int64_t uni = 16 * H + 20 * (n + 1);
     const int64_t meta = 16 * n + 4 * (T + n + 1);
     const int64_t Tpad = (T + 15) / 16 * 16;
-    const int64_t work = 2 * Tpad + 8 * V + 16 * ((T + OUT_TILE_MIN - 1) / OUT_TILE_MIN) + 12 * out_rec_count(T) + 8 * out_warp_count(T) +
+    const int64_t work = 2 * Tpad + 8 * V + 16 * ((T + OUT_TILE_MIN - 1) / OUT_TILE_MIN) + 16 * ((T + OUT_TILE_MIN - 1) / OUT_TILE_MIN / 1024 + 1) + 8 * out_rec_count(T) + 8 * out_warp_count(T) +
                          4 * T + 4 * (T + 1) + 24 * T + 256;
     const int64_t lepp = 16 * ((T + 1023) / 1024 + 1) + 8;  // path-scan totals of the Lepp primitive
     return arena + uni + meta + work + lepp + 64 * 256;      // + small allocations and their rounding
