@@ -240,7 +240,7 @@ def algorithmic_bytes(T, V, NF, P):
         "tile_scan": 0,
         "poly_list": 8 * NF + 8 * P,
         "batch_pack": 0,
-        "batch_unpack": 0,
+        "batch_meta": 0,
     }
     assert sum(per_stage.values()) == total
     return total, per_stage
@@ -786,7 +786,7 @@ def run_batched(args):
 
     total_alg, per_stage = algorithmic_bytes(T, V, NF, P)
     per_stage["batch_pack"] = 16 * H                 # local origin/twin in, union out
-    per_stage["batch_unpack"] = 48 * T               # union next/prev in, local out
+    per_stage["batch_meta"] = 0                      # serving only
     dominant = max(stage_ms, key=stage_ms.get)
     peak, peak_kind = measured_peaks()
     ach = per_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9

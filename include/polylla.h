@@ -217,9 +217,9 @@ int polylla_generate_host(polylla_ctx *ctx, const polylla_host_mesh *in,
  * polylla_stage_name gives the name of stage i: the seven kernels of the
  * method ("longest_edge", "label_relink", "chords", "chord_links",
  * "poly_count", "tile_scan", "poly_list"), then "batch_pack" and
- * "batch_unpack".  polylla_launch_count gives the number of kernels the
- * last generate launched (7 for a mesh, 12 for a batch, 13 for a served
- * batch).
+ * "batch_meta" (the serving loop's per-mesh metadata).
+ * polylla_launch_count gives the number of kernels the last generate
+ * launched (7 for a mesh, 9 for a batch, 10 for a served batch).
  */
 int polylla_set_timing(polylla_ctx *ctx, int32_t enable);
 int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
@@ -273,7 +273,7 @@ int polylla_batch_polygon_offsets(polylla_ctx *ctx, const int32_t **poly_offset)
  * context (its kernels, with the current launch settings) into a CUDA graph
  * on stream (which must not be NULL, the legacy stream cannot be captured);
  * from then on polylla_generate launches that graph, one launch instead of
- * 7 or 12, untimed.  Changing the launch settings (polylla_set_tuning,
+ * 7 or 9, untimed.  Changing the launch settings (polylla_set_tuning,
  * polylla_autotune) or polylla_release_graph drops the graph.  The graph
  * reads and writes the same device arrays as the captured generate.
  */

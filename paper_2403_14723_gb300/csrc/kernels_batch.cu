@@ -1,8 +1,9 @@
 // Batches of independent meshes (no counterpart in the paper, whose method
 // takes one mesh): the stage kernels run once over the batch's union, a
 // single mesh whose connected components are the batch's meshes.  Packing
-// renumbers each mesh's local indices into the union; unpacking writes the
-// relinked next/prev back in local indices and finds each mesh's polygons.
+// renumbers each mesh's local indices into the union; the relink and repair
+// kernels write the relinked next/prev in local indices too, and the listing
+// kernel writes local seeds and each mesh's first polygon.
 //
 // The union keeps every order the method depends on within a mesh: interior
 // half-edges of mesh i are shifted by 3 t_off[i], its border half-edges go
@@ -255,79 +256,6 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t
 }
 
 // ===========================================================================
-// k_batch_unpack: relinked next/prev of every interior union half-edge back
-// into the mesh's local arrays (a relinked successor or predecessor of an
-// interior half-edge is an interior half-edge of the same mesh).  Loads of
-// all items first, then the stores, as in the pack.
-// ===========================================================================
-__global__ void __launch_bounds__(BP_THREADS) k_batch_unpack(BatchView b, const int32_t *u_next,
-                                                             const int32_t *u_prev) {
-    __shared__ PackTable tb;
-    const int32_t HI = 3 * b.T_tot;
-    const int32_t base = (int32_t)blockIdx.x * BP_SPAN;
-    const int32_t end = min(base + BP_SPAN, HI);
-    const bool tabled = pack_table(b, false, base, end, tb);
-    int32_t nx[BP_ITEMS], pv[BP_ITEMS];
-#pragma unroll
-    for (int k = 0; k < BP_ITEMS; k++) {
-        const int32_t x = base + k * BP_THREADS + (int32_t)threadIdx.x;
-        if (x < end) {
-            nx[k] = u_next[x];
-            pv[k] = u_prev[x];
-        }
-    }
-    int32_t j = 0;
-#pragma unroll
-    for (int k = 0; k < BP_ITEMS; k++) {
-        const int32_t x = base + k * BP_THREADS + (int32_t)threadIdx.x;
-        if (x >= end) break;
-        int32_t shift, g;
-        if (tabled) {
-            while (tb.start[j + 1] <= x) j++;
-            shift = tb.t3[j];
-            g = x + tb.to_local[j];
-        } else {
-            const int32_t m = seg_of(b.t_off, b.n, x / 3);
-            shift = 3 * b.t_off[m];
-            g = b.h_off[m] + (x - shift);
-        }
-        b.next[g] = nx[k] - shift;
-        b.prev[g] = pv[k] - shift;
-    }
-}
-
-// ===========================================================================
-// k_batch_ranges: poly_off[i] = number of polygons whose (union) seed lies
-// below mesh i's first half-edge, i.e. mesh i owns polygons
-// [poly_off[i], poly_off[i+1]); poly_off[n] = P.
-// k_batch_seeds: then each seed becomes local; a polygon's list starts at its
-// seed and the emitted lists are already local, so seed = he_list[offsets[p]].
-// ===========================================================================
-__global__ void k_batch_ranges(BatchView b, const int32_t *seeds, const DevCtrl *ctrl, int32_t *poly_off) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > b.n) return;
-    const int32_t P = ctrl->n_polygons;
-    if (i == b.n) {
-        poly_off[i] = P;
-        return;
-    }
-    const int32_t key = 3 * b.t_off[i];
-    int32_t lo = 0, hi = P;  // first p with seeds[p] >= key
-    while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (seeds[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    poly_off[i] = lo;
-}
-
-__global__ void k_batch_seeds(int32_t *seeds, const int32_t *offsets, const int32_t *he_list, const DevCtrl *ctrl) {
-    const int32_t P = ctrl->n_polygons;
-    for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-        seeds[p] = he_list[offsets[p]];
-}
-
-// ===========================================================================
 // k_batch_meta (serving): per mesh i, meta[4i..4i+3] = {P_i, N_F,i, first
 // polygon, first CSR entry}, and each mesh's offsets rebased to start at 0
 // in local_offsets[poly_off[i] + i .. poly_off[i+1] + i] (P_i + 1 entries),
@@ -378,16 +306,6 @@ void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, i
     }
     const int32_t blocks = (HI + BP_SPAN - 1) / BP_SPAN + (HB + BP_SPAN - 1) / BP_SPAN;
     k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad, input_err, 0);
-}
-
-void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s) {
-    const int32_t blocks = (3 * b.T_tot + BP_SPAN - 1) / BP_SPAN;
-    k_batch_unpack<<<blocks, BP_THREADS, 0, s>>>(b, u.next, u.prev);
-}
-
-void launch_batch_ranges(const BatchView &b, const Work &w, int32_t *poly_off, cudaStream_t s) {
-    k_batch_ranges<<<(b.n + 1 + 255) / 256, 256, 0, s>>>(b, w.seeds, w.ctrl, poly_off);
-    k_batch_seeds<<<w.persistent_blocks, 256, 0, s>>>(w.seeds, w.offsets, w.he_list, w.ctrl);
 }
 
 }  // namespace polylla

@@ -262,7 +262,9 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 // Stages 2-4 fused: frontier labels (Algorithm 3 / 9), seeds (Algorithm 4 /
 // 10) and the relink of every frontier half-edge (Section 4.2; the per-half-
 // edge form of Algorithm 12).  A CTA of NT threads takes NT * IPT
-// consecutive triangles, IPT per thread (strided: triangle t0 + q NT + tid).
+// consecutive triangles, IPT per thread (strided: triangle t0 + q NT + tid);
+// with BATCH (a batch's union) it also writes every link in the meshes' own
+// indices and arrays.
 //
 //   F0[e] = border(e) or (not LE[e] and not LE[twin e])
 //   seed  = the triangle's longest half-edge e when it is the smaller half of
@@ -297,13 +299,14 @@ void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
 // ===========================================================================
 __device__ __forceinline__ int32_t div3(int32_t x) { return (int32_t)((uint32_t)x / 3u); }
 
-template <int NT, int IPT>
+template <int NT, int IPT, bool BATCH>
 __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m, Work w) {
     constexpr int TT = NT * IPT;  // triangles per CTA
     static_assert(IPT >= 1 && IPT <= 4, "a thread's flag bytes fit one 32-bit word");
     __shared__ __align__(16) int32_t s_nx[3 * TT];
     __shared__ __align__(16) int32_t s_pv[3 * TT];
     __shared__ int4 s_task[NT / 32][96 * IPT];
+    __shared__ int32_t s_m0;  // batches: the mesh of the CTA's first triangle
     const int32_t t0 = blockIdx.x * TT;
     const int32_t nT = min(TT, m.T - t0);
     const int32_t eb = 3 * t0;
@@ -311,6 +314,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
     const int32_t HI = 3 * m.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t below = (1u << lane) - 1u;
+    if (BATCH && threadIdx.x == 0) s_m0 = seg_of(w.loc_t_off, w.loc_n, t0);
     uint32_t fls = 0;  // byte q: flags of triangle t0 + q NT + tid
     uint32_t total = 0;
 #pragma unroll
@@ -404,7 +408,15 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
         s_nx[e - eb] = x;
         const uint32_t dx = (uint32_t)(x - eb);
         if (dx < (uint32_t)nE) s_pv[dx] = e;
-        else m.prev[x] = e;
+        else {
+            m.prev[x] = e;
+            if (BATCH) {  // e, x lie in one mesh, at or after the CTA's first
+                int32_t mj = s_m0;
+                while (mj + 1 < w.loc_n && 3 * __ldg(w.loc_t_off + mj + 1) <= e) mj++;
+                const int32_t sh = 3 * __ldg(w.loc_t_off + mj);
+                w.loc_prev[__ldg(w.loc_h_off + mj) + (x - sh)] = e - sh;
+            }
+        }
         if (x == tk.y) {
             const int32_t sl = atomicAdd(&w.ctrl->n_tips, 1);
             if (sl < w.tip_cap) w.tips[sl] = tk.y;
@@ -440,6 +452,21 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
         const int32_t v = s_pv[i];
         if (v >= 0) m.prev[eb + i] = v;
     }
+    // in a batch, the same links in the meshes' own indices and arrays (the
+    // CTA's half-edges are consecutive in a mesh's local arrays between mesh
+    // boundaries, so these stores stay coalesced)
+    if (BATCH) {
+        int32_t mj = s_m0;
+        for (int i = threadIdx.x; i < nE; i += NT) {
+            const int32_t x = eb + i;
+            while (mj + 1 < w.loc_n && 3 * __ldg(w.loc_t_off + mj + 1) <= x) mj++;
+            const int32_t sh = 3 * __ldg(w.loc_t_off + mj);
+            const int32_t g = __ldg(w.loc_h_off + mj) + (x - sh);
+            w.loc_next[g] = s_nx[i] - sh;
+            const int32_t v = s_pv[i];
+            if (v >= 0) w.loc_prev[g] = v - sh;
+        }
+    }
 }
 
 // launch configurations: (triangles per CTA, triangles per thread)
@@ -463,12 +490,14 @@ int relink_configure() { return 0; }  // static shared memory only
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
 #define X(N, I)                                                                      \
     if (w.rl_tile == N * I && w.rl_items == I) {                                     \
-        k_label_relink<N, I><<<(m.T + N * I - 1) / (N * I), N, 0, s>>>(m, w);        \
+        if (w.loc_n > 0) k_label_relink<N, I, true><<<(m.T + N * I - 1) / (N * I), N, 0, s>>>(m, w);  \
+        else k_label_relink<N, I, false><<<(m.T + N * I - 1) / (N * I), N, 0, s>>>(m, w);        \
         return;                                                                      \
     }
     RELINK_CONFIGS(X)
 #undef X
-    k_label_relink<128, 1><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
+    if (w.loc_n > 0) k_label_relink<128, 1, true><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
+    else k_label_relink<128, 1, false><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
 }
 
 }  // namespace polylla

@@ -248,11 +248,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(MeshView m, Work w, 
     w.offsets[P] = (int32_t)NF;
     w.ctrl->n_polygons = (int32_t)P;
     w.ctrl->n_frontier = (int32_t)NF;
+    // in a batch, P closes the ranges (and starts the meshes without triangles
+    // at the end, which no lane holds)
+    for (int32_t j = w.loc_n; w.loc_n > 0 && j >= 0 && __ldg(w.loc_t_off + j) >= m.T; j--) w.loc_poly_off[j] = (int32_t)P;
     if (w.input_err && *w.input_err) atomicOr(&w.ctrl->error, DEV_ERR_INPUT);
 }
 
 // ===========================================================================
-// k_poly_list<TILE, NT>: one CTA per tile.  Thread 0 bulk-copies the tile's
+// k_poly_list<TILE, NT, BATCH>: one CTA per tile (BATCH: the mesh is a
+// batch's union, whose seeds, lists and per-mesh polygon ranges are written
+// in each mesh's own indices).  Thread 0 bulk-copies the tile's
 // next and origin.  Then every warp works on its own: its first polygon and
 // entry are the scanned total of the tiles before its tile plus the totals
 // of the warps before it in the tile; every minimum of its lanes writes its
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(MeshView m, Work w, 
 // directly), which the warp then stores, one contiguous range of he_list
 // and v_list, coalesced.
 // ===========================================================================
-template <int TILE, int NT>
+template <int TILE, int NT, bool BATCH>
 __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     constexpr int IPT = TILE / NT;
     constexpr int E = 3 * TILE;
@@ -322,20 +327,40 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     int32_t *st_he = s_stage + wid * 2 * WCAP;
     int32_t *st_v = st_he + WCAP;
     const int32_t lt0 = (int32_t)threadIdx.x * IPT;
+    // in a batch, the mesh of the warp's first triangle (one search per
+    // warp); each lane steps forward from it to the meshes of its minima
+    int32_t mi = 0;
+    if (BATCH) {
+        const int32_t tw0 = t0 + (int32_t)(threadIdx.x & ~31u) * IPT;
+        mi = __shfl_sync(0xffffffffu, lane == 0 ? seg_of(w.loc_t_off, w.loc_n, min(tw0, m.T - 1)) : 0, 0);
+    }
+    // in a batch, the lane holding a mesh's first triangle writes the mesh's
+    // first polygon: its own first polygon plus its minima before the mesh
+    if (BATCH && lt0 < nt) {
+        const int32_t lf = t0 + lt0, le_ = t0 + min(lt0 + IPT, nt);  // the lane's triangles [lf, le_)
+        int32_t j = mi;
+        while (j < w.loc_n && __ldg(w.loc_t_off + j) < lf) j++;
+        for (; j < w.loc_n; j++) {
+            const int32_t tj = __ldg(w.loc_t_off + j);
+            if (tj >= le_) break;
+            const uint32_t below = (1u << (3 * (tj - lf))) - 1u;  // minima of the lane's earlier triangles
+            w.loc_poly_off[j] = p + __popc(minmask & below);
+        }
+    }
     while (minmask) {
         const int b = __ffs(minmask) - 1;
         minmask &= minmask - 1u;
         const int32_t e = eb + 3 * (lt0 + b / 3) + b % 3;
-        w.seeds[p] = e;
+        // in a batch, seeds and lists are written in the mesh's own indices
+        int32_t she = 0, sv = 0;
+        if (BATCH) {
+            while (mi + 1 < w.loc_n && __ldg(w.loc_t_off + mi + 1) <= e / 3) mi++;
+            she = 3 * __ldg(w.loc_t_off + mi);
+            sv = __ldg(w.loc_v_off + mi);
+        }
+        w.seeds[p] = e - she;
         w.offsets[p] = (int32_t)NF0 + pos;
         p++;
-        // in a batch, lists are written in the mesh's own indices
-        int32_t she = 0, sv = 0;
-        if (w.loc_n > 0) {
-            const int32_t i = seg_of(w.loc_t_off, w.loc_n, e / 3);
-            she = 3 * __ldg(w.loc_t_off + i);
-            sv = __ldg(w.loc_v_off + i);
-        }
         int32_t x = e;
         int32_t guard = 0;
         do {  // k_poly_count's walk came back to e: this loop ends
@@ -392,7 +417,9 @@ int polygons_configure() {
 #define X(TL, N)                                                                                             \
     if (cudaFuncSetAttribute(k_poly_count<TL, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,               \
                              (int)count_smem<TL>()) != cudaSuccess ||                                        \
-        cudaFuncSetAttribute(k_poly_list<TL, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+        cudaFuncSetAttribute(k_poly_list<TL, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                             (int)list_smem<TL>()) != cudaSuccess ||                                         \
+        cudaFuncSetAttribute(k_poly_list<TL, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
                              (int)list_smem<TL>()) != cudaSuccess)                                           \
         return -1;
     POLYGON_CONFIGS(X)
@@ -405,7 +432,7 @@ int polygons_blocks_per_sm(int32_t tile, int32_t items) {
     int nb = 0;
 #define X(TL, N)                                                                                          \
     if (tile == TL && items == TL / N) {                                                                  \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_poly_list<TL, N>, N, list_smem<TL>()) != \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_poly_list<TL, N, false>, N, list_smem<TL>()) != \
             cudaSuccess)                                                                                  \
             nb = 0;                                                                                       \
     }
@@ -436,12 +463,14 @@ void launch_tile_scan(const MeshView &m, const Work &w, cudaStream_t s) {
 void launch_poly_list(const MeshView &m, const Work &w, cudaStream_t s) {
 #define X(TL, N)                                                                            \
     if (w.out_tile == TL && w.out_items == TL / N) {                                        \
-        k_poly_list<TL, N><<<(m.T + TL - 1) / TL, N, list_smem<TL>(), s>>>(m, w);           \
+        if (w.loc_n > 0) k_poly_list<TL, N, true><<<(m.T + TL - 1) / TL, N, list_smem<TL>(), s>>>(m, w); \
+        else k_poly_list<TL, N, false><<<(m.T + TL - 1) / TL, N, list_smem<TL>(), s>>>(m, w);      \
         return;                                                                             \
     }
     POLYGON_CONFIGS(X)
 #undef X
-    k_poly_list<2048, 512><<<(m.T + 2047) / 2048, 512, list_smem<2048>(), s>>>(m, w);
+    if (w.loc_n > 0) k_poly_list<2048, 512, true><<<(m.T + 2047) / 2048, 512, list_smem<2048>(), s>>>(m, w);
+    else k_poly_list<2048, 512, false><<<(m.T + 2047) / 2048, 512, list_smem<2048>(), s>>>(m, w);
 }
 
 }  // namespace polylla

@@ -73,7 +73,24 @@ void launch_chords(const MeshView &m, const Work &w, cudaStream_t s) {
 // Every half-edge whose next or prev changes gets the walk-start mark (the
 // polygon kernel needs the marks to be a superset of the polygon minima).
 // ===========================================================================
+// in a batch, a union link a -> b (both interior, one mesh) in the mesh's own
+// next/prev as well
+struct LocalLinks {
+    int32_t sh, ho;  // 3 t_off and h_off of the mesh; ho < 0: a single mesh
+    __device__ void link(const Work &w, int32_t a, int32_t b) const {
+        if (ho < 0) return;
+        w.loc_next[ho + (a - sh)] = b - sh;
+        w.loc_prev[ho + (b - sh)] = a - sh;
+    }
+};
+
 __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, int32_t c, int32_t HI) {
+    LocalLinks loc{0, -1};
+    if (w.loc_n > 0) {
+        const int32_t mj = seg_of(w.loc_t_off, w.loc_n, tri_of(c));
+        loc.sh = 3 * __ldg(w.loc_t_off + mj);
+        loc.ho = __ldg(w.loc_h_off + mj);
+    }
     // clockwise neighbour
     int32_t tc = __ldg(m.twin + c);
     int32_t y = nx_of(tc);
@@ -84,6 +101,7 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
     }
     m.next[tc] = y;
     m.prev[y] = tc;
+    loc.link(w, tc, y);
     set_start(w.flags, tc);
     set_start(w.flags, y);
     // counter-clockwise neighbour; reaching a border half-edge z means the
@@ -99,6 +117,7 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
     // twin(z) == pv
     m.next[pv] = c;
     m.prev[c] = pv;
+    loc.link(w, pv, c);
     set_start(w.flags, pv);
     set_start(w.flags, c);
 }

@@ -15,14 +15,14 @@ using namespace polylla;
 namespace {
 
 constexpr int kCore = 7;     // the method's kernels, on one mesh or a batch's union
-constexpr int kStages = 9;   // + batch packing and unpacking
-constexpr int kPack = 7, kUnpack = 8;
+constexpr int kStages = 9;   // + batch packing and serving metadata
+constexpr int kPack = 7, kMeta = 8;
 const char *kStageNames[kStages] = {
     "longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan", "poly_list",
-    "batch_pack", "batch_unpack",
+    "batch_pack", "batch_meta",
 };
 constexpr int kKernels = 7;        // one kernel per stage
-constexpr int kBatchKernels = 5;   // pack (interior, border); unpack; ranges (two kernels)
+constexpr int kBatchKernels = 2;   // pack (interior, border)
 
 }  // namespace
 
@@ -406,8 +406,9 @@ int polylla_create_host(polylla_ctx **out, int32_t n_vertices, int32_t n_triangl
 }  // extern "C"
 
 // Enqueue one whole run on s: for a batch, packing, then the method's
-// stages on the union, then unpacking; with timing, an event pair around
-// every stage.
+// stages on the union (which also write each mesh's own next/prev, seeds
+// and polygon ranges), then, when serving, the per-mesh metadata; with
+// timing, an event pair around every stage.
 static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
     for (int i = 0; i < kStages; i++) c->stage_ran[i] = false;
     auto begin = [&](int i) -> cudaError_t {
@@ -433,11 +434,11 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
         if (i == 3 && c->record_after_links) CK(cudaEventRecord(c->record_after_links, s));
     }
     if (c->is_batch) {
-        CK(begin(kUnpack));
-        launch_batch_unpack(c->bv, c->mesh, s);
-        launch_batch_ranges(c->bv, c->w, c->poly_off, s);
+        CK(begin(kMeta));
+        // the relink and repair kernels wrote the meshes' own next/prev and
+        // the listing kernel their seeds and polygon ranges
         if (c->serve) launch_batch_meta(c->bv, c->w, c->poly_off, c->local_offsets, c->meta, s);
-        CK(end(kUnpack));
+        CK(end(kMeta));
     }
     c->launches = kKernels + (c->is_batch ? kBatchKernels : 0) + (c->serve ? 1 : 0);
     CK(cudaGetLastError());
@@ -610,7 +611,7 @@ int polylla_get_stage_times(polylla_ctx *c, float *ms, int32_t n) {
     for (int i = 0; i < kStages; i++)
         if (c->stage_ran[i]) last = i;
     if (last < 0) return 0;
-    CK(cudaEventSynchronize(c->ev_end[c->is_batch ? kUnpack : kCore - 1]));
+    CK(cudaEventSynchronize(c->ev_end[c->is_batch ? kMeta : kCore - 1]));
     const int k = n < kStages ? n : kStages;
     for (int i = 0; i < k; i++) {
         float t = 0.f;
@@ -683,6 +684,10 @@ int polylla_batch_create(polylla_ctx **out, const polylla_batch *b, const polyll
     if (!rc) {
         c->w.loc_t_off = bv.t_off;
         c->w.loc_v_off = bv.v_off;
+        c->w.loc_h_off = bv.h_off;
+        c->w.loc_next = bv.next;
+        c->w.loc_prev = bv.prev;
+        c->w.loc_poly_off = c->poly_off;
         c->w.loc_n = n;
         if (!opt || opt->validate) {
             // range checks of every local index while packing all four
@@ -929,6 +934,10 @@ int serve_reserve(polylla_ctx **out, int32_t n_cap, int32_t V_cap, int32_t T_cap
     }
     c->w.loc_t_off = c->bv.t_off;
     c->w.loc_v_off = c->bv.v_off;
+    c->w.loc_h_off = c->bv.h_off;
+    c->w.loc_next = c->bv.next;
+    c->w.loc_prev = c->bv.prev;
+    c->w.loc_poly_off = c->poly_off;
     *out = c;
     return POLYLLA_OK;
 }

@@ -81,6 +81,10 @@ struct Work {
     // batches: the emitted he_list / v_list are made mesh-local when set
     const int32_t *loc_t_off;    // [loc_n+1] triangle offset of each mesh
     const int32_t *loc_v_off;    // [loc_n+1] vertex offset of each mesh
+    const int32_t *loc_h_off;    // [loc_n+1] half-edge offset of each mesh in the local arrays
+    int32_t *loc_next;           // the meshes' own next/prev (local indices), written
+    int32_t *loc_prev;           //   by the relink and repair kernels
+    int32_t *loc_poly_off;       // [loc_n+1] first polygon of each mesh, P at the end
     int32_t loc_n;               // number of meshes (0: a single mesh)
     int32_t *input_err;          // batches: set by the pack on an out-of-range index
 };
@@ -235,8 +239,6 @@ void launch_lepp_paths(const MeshView &m, const Work &w, const int32_t *tri, int
 // batches (kernels_batch.cu)
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
                        int32_t *bad, int32_t *input_err, cudaStream_t s);
-void launch_batch_unpack(const BatchView &b, const MeshView &u, cudaStream_t s);
-void launch_batch_ranges(const BatchView &b, const Work &w, int32_t *poly_off, cudaStream_t s);  // two kernels
 void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_off, int32_t *local_offsets,
                        int32_t *meta, cudaStream_t s);
 

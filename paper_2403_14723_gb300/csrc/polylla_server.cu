@@ -6,7 +6,7 @@
 // order, as many waiting requests as fit the slot's capacity (meshes,
 // triangles, vertices, half-edges), copies their coords, origin and twin
 // into the slot's device arena (the method never reads next/prev), runs the
-// batch (pack, the method's stages, unpack, per-mesh metadata) and moves
+// batch (pack, the method's stages, per-mesh metadata) and moves
 // the per-mesh metadata to pinned host memory.  When that has landed it
 // copies each request's CSR slices and interior next/prev back into the
 // request's host buffers (border entries are the input's, copied on the
@@ -52,8 +52,9 @@ constexpr int64_t kLaneBatch = 16;        // the lane slot holds 16 requests of 
 constexpr size_t kLogKeep = 65536;  // completed batches kept for polylla_server_get_batch_log
 constexpr int32_t kLaneDefault = 65536;  // lane_triangles when the option is 0
 constexpr double kStealSeconds = 0.005;  // a lane request older than this may join any batch
-constexpr int32_t kLaunchesCE = 18;      // per batch: offsets, 16 of the run, metadata out
-constexpr int32_t kLaunchesLane = 19;    // per lane batch: gather, offsets, 16 of the run, scatter
+// kernels per batch; the run is 10 (pack 2, the method 7, metadata 1)
+constexpr int32_t kLaunchesCE = 12;      // per batch: offsets, the run, metadata out
+constexpr int32_t kLaunchesLane = 13;    // per lane batch: gather, offsets, the run, scatter
 
 struct Req {
     polylla_request r{};

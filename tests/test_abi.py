@@ -52,7 +52,7 @@ def test_status_strings_without_gpu(lib_path):
     assert lib.polylla_stage_count() == 9
     names = [lib.polylla_stage_name(i).decode() for i in range(9)]
     assert names == ["longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan",
-                     "poly_list", "batch_pack", "batch_unpack"]
+                     "poly_list", "batch_pack", "batch_meta"]
 
 
 def test_null_arguments_rejected_without_gpu(lib_path):

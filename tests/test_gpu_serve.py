@@ -75,7 +75,7 @@ def test_served_requests_match_oracle_alone_and_in_the_mix():
         for k in ("n_slots", "slot_triangles", "lane_triangles", "lane_slot_triangles"):
             assert st[k] == plan[k], k
         assert any(b["lane"] == 1 for b in log) and any(b["lane"] == 0 for b in log)
-        assert st["launches"] == 19 * st["lane_batches"] + 18 * (st["batches"] - st["lane_batches"])
+        assert st["launches"] == 13 * st["lane_batches"] + 12 * (st["batches"] - st["lane_batches"])
 
 
 def test_copy_paths_give_identical_results():
