@@ -334,8 +334,8 @@ int polylla_tuning_cache_clear(void);
  * polylla_get_labels then hold this frontier), next/prev around the chord
  * ends are relinked as by the repair, and polylla_get_polygons returns the
  * convex polygons (same canonical order).  Every corner of the result
- * turns by at most a half turn.  The first call allocates the chord list
- * (4 x 3T bytes); later calls allocate nothing.  Single-mesh contexts only
+ * turns by at most a half turn.  The first call allocates its chord and
+ * reflex-corner lists (2 x 4 x 3T bytes); later calls allocate nothing.  Single-mesh contexts only
  * (INVALID_ARGUMENT on a batch).  Asynchronous; device errors through
  * polylla_last_error.  polylla_convex_chords gives the chosen half-edges of
  * the last convexify (device pointer owned by the context, *n of them, each

@@ -74,20 +74,6 @@ void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s) {
 // edges, the float64 argmax is the same edge and has no tie.
 // ===========================================================================
 
-__device__ __forceinline__ float trunc_to_f32(double v, uint32_t &bad) {
-    uint32_t hi = (uint32_t)__double2hiint(v);
-    uint32_t lo = (uint32_t)__double2loint(v);
-    uint32_t mag = hi & 0x7FFFFFFFu;
-    // biased float64 exponent must lie in [897, 1083]: |v| in [2^-126, 2^60)
-    bad |= (uint32_t)((mag - (897u << 20)) >= ((1084u - 897u) << 20));
-    // (hi:lo) << 3 puts the low 9 exponent bits at 31..23 and the top 23
-    // significand bits at 22..0; subtracting 384 from that 9-bit field
-    // rebiases 1023 -> 127 for exponents in range
-    uint32_t bits = __funnelshift_l(lo, hi, 3) - (384u << 23);
-    bits |= hi & 0x80000000u;
-    return __uint_as_float(bits);
-}
-
 struct EdgeF32 {
     float d;   // D^
     float b;   // error bound B

@@ -60,7 +60,8 @@ struct polylla_ctx {
     cudaEvent_t record_after_links = nullptr;  // enqueue: recorded after stage 3
     // convexification: its chord list (allocated by the first call) and count
     int32_t *cv_list = nullptr;
-    int32_t *cv_count = nullptr;
+    int32_t *cv_count = nullptr;   // [2]: chords, reflex corners
+    int32_t *cv_reflex = nullptr;
     int32_t cv_cap = 0;
     // captured generate (polylla_capture_graph)
     cudaGraph_t graph = nullptr;
@@ -840,22 +841,25 @@ int polylla_convexify(polylla_ctx *c, polylla_stream stream) {
     if (!c || c->is_batch) return POLYLLA_ERR_INVALID_ARGUMENT;
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->cv_list) {
-        // every chord is a distinct non-frontier interior half-edge: 3T bound
+        // every chord is a distinct non-frontier interior half-edge and
+        // every reflex corner a frontier one: 3T bounds
         void *p = nullptr;
         int rc = dev_alloc(c, &p, sizeof(int32_t) * 3 * (size_t)c->mesh.T);
         if (rc) return rc;
         c->cv_list = (int32_t *)p;
-        if ((rc = dev_alloc(c, &p, sizeof(int32_t)))) return rc;
+        if ((rc = dev_alloc(c, &p, sizeof(int32_t) * 3 * (size_t)c->mesh.T))) return rc;
+        c->cv_reflex = (int32_t *)p;
+        if ((rc = dev_alloc(c, &p, 2 * sizeof(int32_t)))) return rc;
         c->cv_count = (int32_t *)p;
         c->cv_cap = 3 * c->mesh.T;
     }
     c->last_stream = s;
     const int32_t tile = polygons_config_valid(c->w.out_tile, c->w.out_items) ? c->w.out_tile : OUT_TILE_DEFAULT;
     const size_t n_tiles = ((size_t)c->mesh.T + tile - 1) / tile;
-    CK(cudaMemsetAsync(c->cv_count, 0, sizeof(int32_t), s));
+    CK(cudaMemsetAsync(c->cv_count, 0, 2 * sizeof(int32_t), s));
     CK(cudaMemsetAsync(c->w.tile_state, 0, sizeof(unsigned long long) * n_tiles, s));
     CK(cudaMemsetAsync(&c->w.ctrl->scan_done, 0, sizeof(int32_t), s));
-    launch_convex_chords(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
+    launch_convex_chords(c->mesh, c->w, c->cv_reflex, c->cv_count + 1, c->cv_list, c->cv_count, c->cv_cap, s);
     launch_convex_mark(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
     launch_chord_links_list(c->mesh, c->w, c->cv_list, c->cv_count, c->cv_cap, s);
     launch_poly_count(c->mesh, c->w, s);

@@ -187,6 +187,25 @@ __device__ __forceinline__ int32_t seg_of(const int32_t *off, int32_t n, int32_t
     return lo;
 }
 
+// ---- float32 filters of float64 decisions -----------------------------------
+// v truncated to float32: the top 23 significand bits, so |v^ - v| <= 2^-23
+// |v^| and |v^| <= |v|, by bit manipulation (no float64 instruction).  A
+// magnitude outside [2^-126, 2^60) (zero included) sets bad: the caller then
+// takes its exact float64 path.
+__device__ __forceinline__ float trunc_to_f32(double v, uint32_t &bad) {
+    uint32_t hi = (uint32_t)__double2hiint(v);
+    uint32_t lo = (uint32_t)__double2loint(v);
+    uint32_t mag = hi & 0x7FFFFFFFu;
+    // biased float64 exponent must lie in [897, 1083]: |v| in [2^-126, 2^60)
+    bad |= (uint32_t)((mag - (897u << 20)) >= ((1084u - 897u) << 20));
+    // (hi:lo) << 3 puts the low 9 exponent bits at 31..23 and the top 23
+    // significand bits at 22..0; subtracting 384 from that 9-bit field
+    // rebiases 1023 -> 127 for exponents in range
+    uint32_t bits = __funnelshift_l(lo, hi, 3) - (384u << 23);
+    bits |= hi & 0x80000000u;
+    return __uint_as_float(bits);
+}
+
 // ---- implicit triangle layout (paper Section 4.2) -------------------------
 __device__ __forceinline__ int32_t tri_of(int32_t e) { return e / 3; }
 __device__ __forceinline__ int32_t loc_of(int32_t e) { return e - 3 * (e / 3); }
@@ -215,8 +234,10 @@ void launch_chord_links(const MeshView &m, const Work &w, cudaStream_t s);
 void launch_chord_links_list(const MeshView &m, const Work &w, const int32_t *list, const int32_t *count,
                              int32_t cap, cudaStream_t s);
 // convexification (kernels_convex.cu)
-void launch_convex_chords(const MeshView &m, const Work &w, int32_t *list, int32_t *count, int32_t cap,
-                          cudaStream_t s);
+// two kernels: the reflex corners into reflex (count n_reflex), then their
+// chords into list (count count); both lists hold at most cap entries
+void launch_convex_chords(const MeshView &m, const Work &w, int32_t *reflex, int32_t *n_reflex, int32_t *list,
+                          int32_t *count, int32_t cap, cudaStream_t s);
 void launch_convex_mark(const MeshView &m, const Work &w, const int32_t *list, const int32_t *count, int32_t cap,
                         cudaStream_t s);
 void launch_poly_count(const MeshView &m, const Work &w, cudaStream_t s);
