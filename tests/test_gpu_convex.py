@@ -81,6 +81,22 @@ def test_convex_parity_exact_grid_and_lattice():
         break
 
 
+def test_convex_parity_near_ties():
+    """Lattice coordinates moved by a few ulps: turn tests close to zero,
+    where the float32 filter must defer to binary64."""
+    done = 0
+    for s in range(6):
+        try:
+            mesh = meshgen.near_tie_delaunay(3000, 80, seed=525 + s)
+        except ValueError:
+            continue
+        assert_convex_parity(mesh, gpu_convex(mesh))
+        done += 1
+        if done == 2:
+            break
+    assert done > 0
+
+
 def test_convex_twice_is_a_fixed_point_and_generate_restores():
     import torch
 
