@@ -227,8 +227,8 @@ def algorithmic_bytes(T, V, NF, P):
     the longest edge reads origin and coords (12T + 16V), the relink reads
     twin and writes next/prev of the frontier (12T + 8 N_F), the listing
     kernel writes the CSR (8 N_F + 8P); the repair kernels, the polygon
-    count (a second read of next) and the batch format kernels move no
-    bytes of B_alg.  The shares sum to B_alg, so a
+    count (a second read of next), the tile scan and the batch metadata
+    move no bytes of B_alg.  The shares sum to B_alg, so a
     kernel's traffic over its share is the bytes it re-reads."""
     total = 24 * T + 16 * V + 16 * NF + 8 * P
     per_stage = {
@@ -239,7 +239,6 @@ def algorithmic_bytes(T, V, NF, P):
         "poly_count": 0,
         "tile_scan": 0,
         "poly_list": 8 * NF + 8 * P,
-        "batch_pack": 0,
         "batch_meta": 0,
     }
     assert sum(per_stage.values()) == total
@@ -785,7 +784,6 @@ def run_batched(args):
         polylla.polylla_destroy(ctx)
 
     total_alg, per_stage = algorithmic_bytes(T, V, NF, P)
-    per_stage["batch_pack"] = 16 * H                 # local origin/twin in, union out
     per_stage["batch_meta"] = 0                      # serving only
     dominant = max(stage_ms, key=stage_ms.get)
     peak, peak_kind = measured_peaks()

@@ -211,15 +211,15 @@ int polylla_generate_host(polylla_ctx *ctx, const polylla_host_mesh *in,
  * Per-stage timing.  With timing enabled, generate records a pair of CUDA
  * events around each stage it runs (on the generate stream);
  * polylla_get_stage_times synchronizes and writes the milliseconds of up to
- * n stages of the last generate (0 for a stage that did not run: the two
- * batch stages on a single mesh), returning how many it wrote, or 0 when
+ * n stages of the last generate (0 for a stage that did not run: the
+ * batch stage on a single mesh), returning how many it wrote, or 0 when
  * the last generate was not timed (timing off, or a captured graph).
  * polylla_stage_name gives the name of stage i: the seven kernels of the
  * method ("longest_edge", "label_relink", "chords", "chord_links",
- * "poly_count", "tile_scan", "poly_list"), then "batch_pack" and
- * "batch_meta" (the serving loop's per-mesh metadata).
+ * "poly_count", "tile_scan", "poly_list"), then "batch_meta" (the serving
+ * loop's per-mesh metadata).
  * polylla_launch_count gives the number of kernels the last generate
- * launched (7 for a mesh, 9 for a batch, 10 for a served batch).
+ * launched (7 for a mesh or a batch, 8 for a served batch).
  */
 int polylla_set_timing(polylla_ctx *ctx, int32_t enable);
 int polylla_get_stage_times(polylla_ctx *ctx, float *ms, int32_t n);
@@ -244,7 +244,8 @@ int polylla_launch_count(polylla_ctx *ctx);
  * as for one mesh of the total size plus 16 bytes per half-edge for the
  * batch's union.  The device arrays are not copied and must stay valid.
  * polylla_generate on a batch context runs the method once over all meshes
- * -- one launch per stage, not one per mesh -- and gives each mesh exactly
+ * -- one launch per stage, not one per mesh, reading each mesh's own
+ * arrays (no copy into the union) -- and gives each mesh exactly
  * what polylla_generate gives it alone: next/prev of its interior half-
  * edges are rewritten in its local indices; polylla_get_polygons returns
  * one CSR for the batch, ordered by mesh and then by seed, with seeds,
@@ -394,7 +395,10 @@ int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t 
  * mesh alone, whatever it was batched with: CSR and next/prev in the
  * mesh's own indices, written to the request's host buffers (capacities as
  * polylla_generate_host).  The host arrays of a request must stay valid
- * and unchanged until it completes.
+ * and unchanged until it completes.  In a copy-engine batch each request
+ * completes as soon as its own results have landed (an event after its
+ * copies out; up to 32 per batch, consecutive requests sharing one beyond
+ * that), not when the whole batch's have.
  *
  * Copies: the copy engines run one direction's copies in issue order across
  * all streams, so a small batch's copies would wait behind a large one's.
@@ -412,11 +416,12 @@ int polylla_lepp_paths(polylla_ctx *ctx, const int32_t *tri, int32_t n, int32_t 
  * kernel.  Pageable requests are served too, through the copy engines.
  *
  * Requests are not layout-checked (that would cost a pass per batch), but
- * every origin and twin is range-checked while a batch is packed: an index
- * outside its mesh is replaced by one inside it, so no kernel reads outside
- * the batch's arrays, and the batch completes with POLYLLA_ERR_INVALID_MESH
- * (every request in it: device errors are per batch).  The same holds for
- * polylla_generate on a batch created without validation.
+ * the longest-edge kernel range-checks every interior origin and twin (the
+ * only entries the method reads): an index outside its mesh is replaced by
+ * one inside it, so no kernel reads outside the batch's arrays, and the
+ * batch completes with POLYLLA_ERR_INVALID_MESH (every request in it:
+ * device errors are per batch).  The same holds for polylla_generate on a
+ * batch created without validation.
  */
 typedef struct polylla_server polylla_server;
 typedef struct {
@@ -557,7 +562,7 @@ void polylla_server_destroy(polylla_server *srv);
  * thread, otherwise POLYLLA_OK or POLYLLA_ERR_CUDA.
  *
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory limits.
  * Every call shares the one array and it keeps the last call's contents:
  * calls that overlap on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.

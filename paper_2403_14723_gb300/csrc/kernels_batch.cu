@@ -1,9 +1,13 @@
 // Batches of independent meshes (no counterpart in the paper, whose method
 // takes one mesh): the stage kernels run once over the batch's union, a
-// single mesh whose connected components are the batch's meshes.  Packing
-// renumbers each mesh's local indices into the union; the relink and repair
+// single mesh whose connected components are the batch's meshes.  A
+// generate reads the meshes' own arrays: the longest-edge kernel checks
+// every interior origin and twin against its mesh and writes the union
+// twins, the listing kernel reads local origins; the relink and repair
 // kernels write the relinked next/prev in local indices too, and the listing
-// kernel writes local seeds and each mesh's first polygon.
+// kernel writes local seeds and each mesh's first polygon.  Packing all four
+// arrays into the union (this file) is done once, at create, for the layout
+// check.
 //
 // The union keeps every order the method depends on within a mesh: interior
 // half-edges of mesh i are shifted by 3 t_off[i], its border half-edges go
@@ -81,15 +85,15 @@ __device__ bool pack_table(const BatchView &b, bool border, int32_t base, int32_
 }
 
 // ===========================================================================
-// k_batch_pack: union origin/twin (and next/prev when given) from the local
-// arrays.  Logical blocks [0, nbI) cover interior union half-edges, the rest
-// the border ones (blk0 offsets the launch, so the border blocks can run on
-// their own); a block tabulates the meshes its range touches and each
+// k_batch_pack (create, for the layout check): union origin/twin (and
+// next/prev when given) from the local arrays.  Logical blocks [0, nbI)
+// cover interior union half-edges, the rest the border ones (blk0 offsets
+// the launch); a block tabulates the meshes its range touches and each
 // element finds its mesh there.  Every origin and twin is range-checked:
 // one outside its mesh is replaced by an index inside it (vertex 0, the
-// mesh's first border half-edge), so no later kernel can leave the mesh,
-// and the run is flagged (input_err); with bad != nullptr (create) next and
-// prev are checked too and bad is set.
+// mesh's first border half-edge), so the layout check that follows cannot
+// leave the mesh, and input_err / bad are set; with bad != nullptr next
+// and prev are checked too.
 // ===========================================================================
 __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t *u_origin, int32_t *u_twin,
                                                            int32_t *u_next, int32_t *u_prev, int32_t *bad,
@@ -177,85 +181,6 @@ __global__ void __launch_bounds__(BP_THREADS) k_batch_pack(BatchView b, int32_t 
 }
 
 // ===========================================================================
-// k_batch_pack4 (generate path, interior only): each thread packs runs of 4
-// consecutive union half-edges and stores them with one 16-byte store per
-// array; the border tail is left to k_batch_pack.
-// ===========================================================================
-constexpr int BP4_RUNS = 2;  // runs of 4 per thread
-constexpr int BP4_SPAN = BP_THREADS * 4 * BP4_RUNS;
-__global__ void __launch_bounds__(BP_THREADS) k_batch_pack4(BatchView b, int32_t *u_origin, int32_t *u_twin,
-                                                            int32_t *input_err) {
-    __shared__ PackTable tb;
-    const int32_t HI = 3 * b.T_tot;
-    const int32_t base = (int32_t)blockIdx.x * BP4_SPAN;
-    const int32_t end = min(base + BP4_SPAN, HI);
-    const bool tabled = pack_table(b, false, base, end, tb);
-    int32_t o[BP4_RUNS][4], tw[BP4_RUNS][4], jj[BP4_RUNS][4];
-    int32_t j = 0, fail = 0;
-#pragma unroll
-    for (int r = 0; r < BP4_RUNS; r++) {
-        const int32_t x0 = base + 4 * (r * BP_THREADS + (int32_t)threadIdx.x);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int32_t x = x0 + q;
-            jj[r][q] = -1;
-            if (x >= end) continue;
-            int32_t g;
-            if (tabled) {
-                while (tb.start[j + 1] <= x) j++;
-                g = x + tb.to_local[j];
-                jj[r][q] = j;
-            } else {
-                const int32_t m = seg_of(b.t_off, b.n, x / 3);
-                g = b.h_off[m] + (x - 3 * b.t_off[m]);
-                jj[r][q] = m;
-            }
-            o[r][q] = b.origin[g];
-            tw[r][q] = b.twin[g];
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < BP4_RUNS; r++) {
-        const int32_t x0 = base + 4 * (r * BP_THREADS + (int32_t)threadIdx.x);
-        int32_t uo[4], ut[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            uo[q] = 0;
-            ut[q] = 0;
-            if (jj[r][q] < 0) continue;
-            int32_t t3, ti3, bo, v0, hi, vi;
-            if (tabled) {
-                const int32_t p = jj[r][q];
-                t3 = tb.t3[p]; ti3 = tb.ti3[p]; bo = tb.bo[p]; v0 = tb.v0[p]; hi = tb.hi[p]; vi = tb.vi[p];
-            } else {
-                const int32_t m = jj[r][q];
-                const int32_t t0 = b.t_off[m], Ti = b.t_off[m + 1] - t0;
-                t3 = 3 * t0; ti3 = 3 * Ti; bo = HI + b.b_off[m] - 3 * Ti; v0 = b.v_off[m];
-                hi = b.h_off[m + 1] - b.h_off[m]; vi = b.v_off[m + 1] - v0;
-            }
-            int32_t ov = o[r][q], tv = tw[r][q];
-            // out-of-range indices are flagged and kept inside the mesh
-            if (ov < 0 || ov >= vi) { ov = 0; fail = 1; }
-            if (tv < 0 || tv >= hi) { tv = ti3; fail = 1; }
-            uo[q] = ov + v0;
-            ut[q] = tv < ti3 ? t3 + tv : bo + tv;
-        }
-        if (x0 + 3 < end) {
-            *reinterpret_cast<int4 *>(u_origin + x0) = make_int4(uo[0], uo[1], uo[2], uo[3]);
-            *reinterpret_cast<int4 *>(u_twin + x0) = make_int4(ut[0], ut[1], ut[2], ut[3]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (x0 + q < end) {
-                    u_origin[x0 + q] = uo[q];
-                    u_twin[x0 + q] = ut[q];
-                }
-        }
-    }
-    if (fail && input_err) atomicOr(input_err, 1);
-}
-
-// ===========================================================================
 // k_batch_meta (serving): per mesh i, meta[4i..4i+3] = {P_i, N_F,i, first
 // polygon, first CSR entry}, and each mesh's offsets rebased to start at 0
 // in local_offsets[poly_off[i] + i .. poly_off[i+1] + i] (P_i + 1 entries),
@@ -288,6 +213,23 @@ __global__ void k_batch_meta(BatchView b, const int32_t *offsets, const int32_t 
     }
 }
 
+// ===========================================================================
+// k_batch_seg (serving, per batch): the mesh table, seg[g] = the mesh of
+// union triangle min(g SEG_SPAN, T - 1), by binary search over the triangle
+// prefix sums.
+// ===========================================================================
+__global__ void k_batch_seg(const int32_t *t_off, int32_t n, int32_t T, int32_t *seg) {
+    const int32_t ns = (int32_t)seg_count(T);
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ns; g += gridDim.x * blockDim.x)
+        seg[g] = seg_of(t_off, n, min(g * SEG_SPAN, T - 1));
+}
+
+void launch_batch_seg(const int32_t *t_off, int32_t n, int32_t T, int32_t *seg, cudaStream_t s) {
+    const int32_t ns = (int32_t)seg_count(T);
+    const int32_t blocks = (ns + 255) / 256;
+    k_batch_seg<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(t_off, n, T, seg);
+}
+
 void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_off, int32_t *local_offsets,
                        int32_t *meta, cudaStream_t s) {
     k_batch_meta<<<w.persistent_blocks, 256, 0, s>>>(b, w.offsets, poly_off, local_offsets, meta);
@@ -296,14 +238,6 @@ void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_of
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
                        int32_t *bad, int32_t *input_err, cudaStream_t s) {
     const int32_t HI = 3 * b.T_tot, HB = b.H_tot - HI;
-    if (!u_next && !bad) {
-        // interior by runs of 4, border by the general kernel (its border blocks only)
-        k_batch_pack4<<<(HI + BP4_SPAN - 1) / BP4_SPAN, BP_THREADS, 0, s>>>(b, u_origin, u_twin, input_err);
-        const int32_t nbI = (HI + BP_SPAN - 1) / BP_SPAN, nbB = (HB + BP_SPAN - 1) / BP_SPAN;
-        if (nbB > 0)
-            k_batch_pack<<<nbB, BP_THREADS, 0, s>>>(b, u_origin, u_twin, nullptr, nullptr, nullptr, input_err, nbI);
-        return;
-    }
     const int32_t blocks = (HI + BP_SPAN - 1) / BP_SPAN + (HB + BP_SPAN - 1) / BP_SPAN;
     k_batch_pack<<<blocks, BP_THREADS, 0, s>>>(b, u_origin, u_twin, u_next, u_prev, bad, input_err, 0);
 }

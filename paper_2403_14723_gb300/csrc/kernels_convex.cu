@@ -82,6 +82,21 @@ __device__ int cross_sign(const double2 *__restrict__ xy, const Pt &a, const Pt 
     return c > 0.0 ? 1 : (c < 0.0 ? -1 : 0);
 }
 
+// A slot at the end of a list shared by the whole grid: the lanes of a warp
+// that reach this call together take consecutive slots with one atomic, so
+// the list's counter sees one atomic per warp and call instead of one per
+// entry (a million same-address atomics serialise in L2).  List order is
+// free: every consumer of these lists treats them as sets.
+__device__ __forceinline__ int32_t append_slot(int32_t *count) {
+    const uint32_t mask = __activemask();
+    const int lane = (int)(threadIdx.x & 31u);
+    const int leader = __ffs(mask) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
 // ===========================================================================
 // The corners: for a frontier half-edge e = 3t + k, v = target(e) is the
 // triangle's vertex k + 1, origin(e) its vertex k, and the corner's other
@@ -110,7 +125,7 @@ __device__ void corner_chords(const MeshView &m, const Work &w, int32_t e, int32
             }
         }
         if (best < 0 || steps > w.max_rot) return;                    // candidates ran out: left reflex
-        const int32_t slot = atomicAdd(count, 1);
+        const int32_t slot = append_slot(count);
         if (slot < cap) list[slot] = best;
         else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
         cur = bp;
@@ -150,7 +165,7 @@ __global__ void __launch_bounds__(256, 4) k_convex_reflex(MeshView m, Work w, in
         for (int k = 0; k < 3; k++) {
             if (!((test >> k) & 1u)) continue;
             if (cross_sign(m.xy, p[k], pw[k], p[k == 2 ? 0 : k + 1]) > 0) {  // v = target(e): vertex k + 1
-                const int32_t slot = atomicAdd(n_reflex, 1);
+                const int32_t slot = append_slot(n_reflex);
                 if (slot < cap) reflex[slot] = e0 + k;
                 else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
             }

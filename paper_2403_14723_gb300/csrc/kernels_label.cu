@@ -99,12 +99,15 @@ __device__ __forceinline__ double sq_len_f64(double2 a, double2 b) {
     return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
-__device__ __noinline__ uint32_t longest_exact(double2 p0, double2 p1, double2 p2, int32_t e0,
-                                               const int32_t *__restrict__ twin) {
+// the exact float64 argmax; tw0..tw2 are the twins of e0, e0 + 1, e0 + 2
+// (equal lengths go to the smaller edge id min(e, twin e))
+__device__ __noinline__ uint32_t longest_exact(double2 p0, double2 p1, double2 p2, int32_t e0, int32_t tw0,
+                                               int32_t tw1, int32_t tw2) {
     double d0 = sq_len_f64(p0, p1);
     double d1 = sq_len_f64(p1, p2);
     double d2 = sq_len_f64(p2, p0);
     double d[3] = {d0, d1, d2};
+    const int32_t tw[3] = {tw0, tw1, tw2};
     uint32_t best = 0;
 #pragma unroll
     for (uint32_t k = 1; k < 3; k++) {
@@ -112,7 +115,7 @@ __device__ __noinline__ uint32_t longest_exact(double2 p0, double2 p1, double2 p
             best = k;
         } else if (d[k] == d[best]) {
             int32_t ek = e0 + (int32_t)k, eb = e0 + (int32_t)best;
-            int32_t tk = twin[ek], tb = twin[eb];
+            int32_t tk = tw[k], tb = tw[best];
             int32_t ik = ek < tk ? ek : tk;
             int32_t ib = eb < tb ? eb : tb;
             if (ik < ib) best = k;
@@ -121,8 +124,10 @@ __device__ __noinline__ uint32_t longest_exact(double2 p0, double2 p1, double2 p
     return best;
 }
 
-__device__ __forceinline__ uint32_t longest_of(double2 p0, double2 p1, double2 p2, int32_t e0,
-                                               const int32_t *__restrict__ twin) {
+// TW: the twins of the triangle's half-edges for the exact path, as
+// tw(k) (read only when the filter cannot decide)
+template <typename TW>
+__device__ __forceinline__ uint32_t longest_of(double2 p0, double2 p1, double2 p2, int32_t e0, TW tw) {
     uint32_t bad = 0;
     const float x0 = trunc_to_f32(p0.x, bad), y0 = trunc_to_f32(p0.y, bad);
     const float x1 = trunc_to_f32(p1.x, bad), y1 = trunc_to_f32(p1.y, bad);
@@ -141,7 +146,7 @@ __device__ __forceinline__ uint32_t longest_of(double2 p0, double2 p1, double2 p
     }
     const float lo = __fsub_rn(dm, bm);
     const bool sure = !bad && lo > __fadd_rn(dA, bA) && lo > __fadd_rn(dB, bB);
-    if (!sure) k = longest_exact(p0, p1, p2, e0, twin);
+    if (!sure) k = longest_exact(p0, p1, p2, e0, tw(0), tw(1), tw(2));
     return k;
 }
 
@@ -218,9 +223,88 @@ __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w)
         for (int q = 0; q < PER; q++) {
             const int32_t lt = lane + 32 * q;
             const int32_t t = t0 + lt;
-            if (t < m.T) w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t, m.twin);
+            const int32_t *__restrict__ twin = m.twin + 3 * t;
+            if (t < m.T)
+                w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t,
+                                              [twin](int k) { return __ldg(twin + k); });
         }
         __syncwarp();  // stage st is refilled next iteration
+    }
+}
+
+// ===========================================================================
+// Stage 1 on a batch, straight from the meshes' own arrays (no packing
+// pass).  One thread per triangle of the union; each thread finds its
+// mesh from the batch's mesh table (the mesh of every 256th triangle) and
+// steps forward over the meshes that end before its triangle.  The
+// local half-edge 3 (t - t_off) + k of triangle t of mesh j sits at
+// h_off + 3 (t - t_off) + k in the concatenated local arrays.  Every origin
+// and twin is range-checked against its mesh: an index outside it is
+// replaced by one inside it (vertex 0; the mesh's first border half-edge,
+// which stops rotations) and the run is flagged, so no later kernel reads
+// outside the mesh.  The thread writes its three half-edges' union twins
+// (interior: 3 t_off + y; border: 3 T + b_off + (y - 3 T_j)), which the
+// later stages walk, and the longest edge as on a single mesh, from the
+// coordinates at the mesh's vertex offset.
+// ===========================================================================
+constexpr int LEB_THREADS = 256;
+constexpr int LEB_ITEMS = 2;  // triangles per thread, their loads in flight together
+
+__global__ void __launch_bounds__(LEB_THREADS) k_longest_edge_batch(MeshView m, Work w) {
+    const int32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gtid < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[gtid] = 0;
+    for (int32_t i = gtid; i < w.n_tile_max; i += gridDim.x * blockDim.x) w.tile_state[i] = 0ull;
+    const int32_t HI = 3 * m.T;
+    const int32_t base = blockIdx.x * (LEB_THREADS * LEB_ITEMS) + (int32_t)threadIdx.x;
+    // per triangle: its mesh's constants, then all loads of origin and twin,
+    // then the checks and union twins, then all coordinate loads
+    int32_t g[LEB_ITEMS], t3[LEB_ITEMS], ti3[LEB_ITEMS], hi[LEB_ITEMS], vi[LEB_ITEMS], v0[LEB_ITEMS];
+#pragma unroll
+    for (int q = 0; q < LEB_ITEMS; q++) {
+        const int32_t t = base + q * LEB_THREADS;
+        g[q] = -1;
+        if (t < m.T) {
+            const int32_t j = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t);
+            t3[q] = 3 * __ldg(w.loc_t_off + j);
+            ti3[q] = 3 * __ldg(w.loc_t_off + j + 1) - t3[q];
+            const int32_t h0 = __ldg(w.loc_h_off + j);
+            hi[q] = __ldg(w.loc_h_off + j + 1) - h0;
+            v0[q] = __ldg(w.loc_v_off + j);
+            vi[q] = __ldg(w.loc_v_off + j + 1) - v0[q];
+            g[q] = h0 + (3 * t - t3[q]);
+        }
+    }
+    int32_t o[LEB_ITEMS][3], tw[LEB_ITEMS][3];
+#pragma unroll
+    for (int q = 0; q < LEB_ITEMS; q++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            o[q][k] = g[q] >= 0 ? __ldg(w.loc_origin + g[q] + k) : 0;
+            tw[q][k] = g[q] >= 0 ? __ldg(w.loc_twin + g[q] + k) : 0;
+        }
+    bool bad = false;
+    double2 p[LEB_ITEMS][3];
+#pragma unroll
+    for (int q = 0; q < LEB_ITEMS; q++) {
+        if (g[q] < 0) continue;
+        const int32_t e0 = 3 * (base + q * LEB_THREADS);
+        const int32_t bo = HI + (g[q] - (e0 - t3[q])) - t3[q] - ti3[q];  // HI + b_off - 3 T_j
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            if ((uint32_t)o[q][k] >= (uint32_t)vi[q]) { o[q][k] = 0; bad = true; }
+            if ((uint32_t)tw[q][k] >= (uint32_t)hi[q]) { tw[q][k] = ti3[q]; bad = true; }
+            tw[q][k] = tw[q][k] < ti3[q] ? t3[q] + tw[q][k] : bo + tw[q][k];
+            w.u_twin[e0 + k] = tw[q][k];
+            p[q][k] = __ldg(m.xy + v0[q] + o[q][k]);
+        }
+    }
+    if (bad) atomicOr(w.input_err, 1);
+#pragma unroll
+    for (int q = 0; q < LEB_ITEMS; q++) {
+        if (g[q] < 0) continue;
+        const int32_t t = base + q * LEB_THREADS;
+        const int32_t *twq = tw[q];
+        w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t, [twq](int k) { return twq[k]; });
     }
 }
 
@@ -234,6 +318,11 @@ int longest_edge_blocks_per_sm(int32_t items) {
 }
 
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
+    if (w.loc_n > 0) {
+        const int32_t span = LEB_THREADS * LEB_ITEMS;
+        k_longest_edge_batch<<<(m.T + span - 1) / span, LEB_THREADS, 0, s>>>(m, w);
+        return;
+    }
     const int32_t tile = 32 * (w.le_items == 4 ? 4 : 2);
     const int32_t n_tiles = (m.T + tile - 1) / tile;
     const int32_t want = (n_tiles + LE_THREADS / 32 - 1) / (LE_THREADS / 32);  // one tile per warp
@@ -300,7 +389,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
     const int32_t HI = 3 * m.T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t below = (1u << lane) - 1u;
-    if (BATCH && threadIdx.x == 0) s_m0 = seg_of(w.loc_t_off, w.loc_n, t0);
+    if (BATCH && threadIdx.x == 0) s_m0 = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t0);
     uint32_t fls = 0;  // byte q: flags of triangle t0 + q NT + tid
     uint32_t total = 0;
 #pragma unroll
@@ -395,8 +484,8 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
         const uint32_t dx = (uint32_t)(x - eb);
         if (dx < (uint32_t)nE) s_pv[dx] = e;
         else {
-            m.prev[x] = e;
-            if (BATCH) {  // e, x lie in one mesh, at or after the CTA's first
+            if (!BATCH) m.prev[x] = e;
+            else {  // e, x lie in one mesh, at or after the CTA's first
                 int32_t mj = s_m0;
                 while (mj + 1 < w.loc_n && 3 * __ldg(w.loc_t_off + mj + 1) <= e) mj++;
                 const int32_t sh = 3 * __ldg(w.loc_t_off + mj);
@@ -434,20 +523,31 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
                 if (4 * i + c < nE) m.next[eb + 4 * i + c] = s_nx[4 * i + c];
         }
     }
-    for (int i = threadIdx.x; i < nE; i += NT) {
+    // (a batch's union prev is never read: its links go to the meshes' own
+    // prev only)
+    for (int i = threadIdx.x; i < nE && !BATCH; i += NT) {
         const int32_t v = s_pv[i];
         if (v >= 0) m.prev[eb + i] = v;
     }
-    // in a batch, the same links in the meshes' own indices and arrays (the
-    // CTA's half-edges are consecutive in a mesh's local arrays between mesh
+    // in a batch, the links in the meshes' own indices and arrays (the CTA's
+    // half-edges are consecutive in a mesh's local arrays between mesh
     // boundaries, so these stores stay coalesced)
     if (BATCH) {
+        // mesh mj spans union half-edges [sh, nb); its local entry of union
+        // x is x + gsh
         int32_t mj = s_m0;
+        int32_t sh = 3 * __ldg(w.loc_t_off + mj);
+        int32_t nb = 3 * __ldg(w.loc_t_off + mj + 1);
+        int32_t gsh = __ldg(w.loc_h_off + mj) - sh;
         for (int i = threadIdx.x; i < nE; i += NT) {
             const int32_t x = eb + i;
-            while (mj + 1 < w.loc_n && 3 * __ldg(w.loc_t_off + mj + 1) <= x) mj++;
-            const int32_t sh = 3 * __ldg(w.loc_t_off + mj);
-            const int32_t g = __ldg(w.loc_h_off + mj) + (x - sh);
+            while (x >= nb && mj + 1 < w.loc_n) {
+                mj++;
+                sh = nb;
+                nb = 3 * __ldg(w.loc_t_off + mj + 1);
+                gsh = __ldg(w.loc_h_off + mj) - sh;
+            }
+            const int32_t g = x + gsh;
             w.loc_next[g] = s_nx[i] - sh;
             const int32_t v = s_pv[i];
             if (v >= 0) w.loc_prev[g] = v - sh;

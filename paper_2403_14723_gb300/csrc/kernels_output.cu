@@ -251,14 +251,21 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(MeshView m, Work w, 
     // in a batch, P closes the ranges (and starts the meshes without triangles
     // at the end, which no lane holds)
     for (int32_t j = w.loc_n; w.loc_n > 0 && j >= 0 && __ldg(w.loc_t_off + j) >= m.T; j--) w.loc_poly_off[j] = (int32_t)P;
-    if (w.input_err && *w.input_err) atomicOr(&w.ctrl->error, DEV_ERR_INPUT);
+    // a batch mesh with an index outside its range (found by the longest-edge
+    // kernel) fails the run; the word is cleared for the next one
+    if (w.input_err && *w.input_err) {
+        atomicOr(&w.ctrl->error, DEV_ERR_INPUT);
+        *w.input_err = 0;
+    }
 }
 
 // ===========================================================================
 // k_poly_list<TILE, NT, BATCH>: one CTA per tile (BATCH: the mesh is a
 // batch's union, whose seeds, lists and per-mesh polygon ranges are written
 // in each mesh's own indices).  Thread 0 bulk-copies the tile's
-// next and origin.  Then every warp works on its own: its first polygon and
+// next and origin (BATCH: next only; the block reads origin from the
+// meshes' own arrays, which hold local vertex ids, into shared memory).
+// Then every warp works on its own: its first polygon and
 // entry are the scanned total of the tiles before its tile plus the totals
 // of the warps before it in the tile; every minimum of its lanes writes its
 // seed and offset and lists its polygon from itself along next (half-edge
@@ -284,16 +291,52 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     const int32_t eb = 3 * t0;
     const uint32_t ne = (uint32_t)(3 * nt);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int32_t s_j0;  // batches: the mesh of the tile's first triangle
     if (threadIdx.x == 0) {
         mbar_init(&s_bar, 1);
         fence_mbar_init();
         const uint32_t be = tile_bytes(nt, 12);
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&s_bar, 2 * be);
+        mbar_arrive_expect_tx(&s_bar, BATCH ? be : 2 * be);
         bulk_load(s_nx, m.next + eb, be, &s_bar);
-        bulk_load(s_org, m.origin + eb, be, &s_bar);
+        if (!BATCH) bulk_load(s_org, m.origin + eb, be, &s_bar);
+        else s_j0 = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t0);
     }
     __syncthreads();
+    if (BATCH) {
+        // origin from the meshes' own arrays (already local vertex ids): union
+        // half-edge x of mesh j is local entry x + h_off[j] - 3 t_off[j].  All
+        // of a thread's addresses first, then all its loads, then the stores,
+        // so its loads are in flight together.
+        constexpr int NK = E / NT;
+        static_assert(E % NT == 0, "whole rounds of the tile's half-edges");
+        int32_t j = s_j0;
+        int32_t jn = 3 * __ldg(w.loc_t_off + j + 1);
+        int32_t sb = __ldg(w.loc_h_off + j) - 3 * __ldg(w.loc_t_off + j);
+        int32_t at[NK];
+#pragma unroll
+        for (int k = 0; k < NK; k++) {
+            const uint32_t d = threadIdx.x + (uint32_t)(k * NT);
+            const int32_t x = eb + (int32_t)d;
+            at[k] = -1;
+            if (d < ne) {
+                while (x >= jn && j + 1 < w.loc_n) {
+                    j++;
+                    jn = 3 * __ldg(w.loc_t_off + j + 1);
+                    sb = __ldg(w.loc_h_off + j) - 3 * __ldg(w.loc_t_off + j);
+                }
+                at[k] = x + sb;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NK; k++) at[k] = at[k] >= 0 ? __ldg(w.loc_origin + at[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < NK; k++) {
+            const uint32_t d = threadIdx.x + (uint32_t)(k * NT);
+            if (d < ne) s_org[d] = at[k];
+        }
+        __syncthreads();
+    }
     const int64_t rec = (int64_t)tile * NT + threadIdx.x;
     const unsigned long long r = w.poly_rec[rec];
     const unsigned long long ex = ((r >> REC_CNT_SHIFT) & REC_CNT_MASK) << 32 | (r & REC_LEN_MASK);
@@ -327,12 +370,12 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     int32_t *st_he = s_stage + wid * 2 * WCAP;
     int32_t *st_v = st_he + WCAP;
     const int32_t lt0 = (int32_t)threadIdx.x * IPT;
-    // in a batch, the mesh of the warp's first triangle (one search per
-    // warp); each lane steps forward from it to the meshes of its minima
+    // in a batch, the mesh of the warp's first triangle (from the mesh
+    // table); each lane steps forward from it to the meshes of its minima
     int32_t mi = 0;
     if (BATCH) {
         const int32_t tw0 = t0 + (int32_t)(threadIdx.x & ~31u) * IPT;
-        mi = __shfl_sync(0xffffffffu, lane == 0 ? seg_of(w.loc_t_off, w.loc_n, min(tw0, m.T - 1)) : 0, 0);
+        mi = __shfl_sync(0xffffffffu, lane == 0 ? mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, min(tw0, m.T - 1)) : 0, 0);
     }
     // in a batch, the lane holding a mesh's first triangle writes the mesh's
     // first polygon: its own first polygon plus its minima before the mesh
@@ -352,11 +395,12 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
         minmask &= minmask - 1u;
         const int32_t e = eb + 3 * (lt0 + b / 3) + b % 3;
         // in a batch, seeds and lists are written in the mesh's own indices
-        int32_t she = 0, sv = 0;
+        // (sb: from a union half-edge to its entry in the local arrays)
+        int32_t she = 0, sb = 0;
         if (BATCH) {
             while (mi + 1 < w.loc_n && __ldg(w.loc_t_off + mi + 1) <= e / 3) mi++;
             she = 3 * __ldg(w.loc_t_off + mi);
-            sv = __ldg(w.loc_v_off + mi);
+            sb = __ldg(w.loc_h_off + mi) - she;
         }
         w.seeds[p] = e - she;
         w.offsets[p] = (int32_t)NF0 + pos;
@@ -366,7 +410,7 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
         do {  // k_poly_count's walk came back to e: this loop ends
             const uint32_t d = (uint32_t)(x - eb);
             const bool in = d < ne;
-            const int32_t v = (in ? s_org[d] : __ldg(m.origin + x)) - sv;
+            const int32_t v = in ? s_org[d] : BATCH ? __ldg(w.loc_origin + x + sb) : __ldg(m.origin + x);
             if (pos < WCAP) {
                 st_he[pos] = x - she;
                 st_v[pos] = v;

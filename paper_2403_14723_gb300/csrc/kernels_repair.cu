@@ -87,7 +87,7 @@ struct LocalLinks {
 __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, int32_t c, int32_t HI) {
     LocalLinks loc{0, -1};
     if (w.loc_n > 0) {
-        const int32_t mj = seg_of(w.loc_t_off, w.loc_n, tri_of(c));
+        const int32_t mj = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, tri_of(c));
         loc.sh = 3 * __ldg(w.loc_t_off + mj);
         loc.ho = __ldg(w.loc_h_off + mj);
     }
@@ -100,7 +100,7 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
         if (++steps > w.max_rot) { atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING); return; }
     }
     m.next[tc] = y;
-    m.prev[y] = tc;
+    if (loc.ho < 0) m.prev[y] = tc;  // a batch's union prev is never read
     loc.link(w, tc, y);
     set_start(w.flags, tc);
     set_start(w.flags, y);
@@ -116,7 +116,7 @@ __device__ __forceinline__ void relink_around(const MeshView &m, const Work &w, 
     }
     // twin(z) == pv
     m.next[pv] = c;
-    m.prev[c] = pv;
+    if (loc.ho < 0) m.prev[c] = pv;
     loc.link(w, pv, c);
     set_start(w.flags, pv);
     set_start(w.flags, c);

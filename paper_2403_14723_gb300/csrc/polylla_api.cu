@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/polylla.h: context lifetime,
 // argument checks, the kernel sequence of polylla_generate, and readback.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -15,14 +16,13 @@ using namespace polylla;
 namespace {
 
 constexpr int kCore = 7;     // the method's kernels, on one mesh or a batch's union
-constexpr int kStages = 9;   // + batch packing and serving metadata
-constexpr int kPack = 7, kMeta = 8;
+constexpr int kStages = 8;   // + the serving loop's per-mesh metadata
+constexpr int kMeta = 7;
 const char *kStageNames[kStages] = {
     "longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan", "poly_list",
-    "batch_pack", "batch_meta",
+    "batch_meta",
 };
 constexpr int kKernels = 7;        // one kernel per stage
-constexpr int kBatchKernels = 2;   // pack (interior, border)
 
 }  // namespace
 
@@ -296,9 +296,16 @@ static int batch_alloc(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t 
     if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->u_twin = (int32_t *)p;
     if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.next = (int32_t *)p;
     if (!rc && (rc = dev_alloc(c, &p, 4 * (size_t)H)) == 0) c->mesh.prev = (int32_t *)p;
+    if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t) * (size_t)seg_count(T))) == 0) c->w.loc_seg = (int32_t *)p;
     if (!rc && (rc = dev_alloc(c, &p, sizeof(int32_t))) == 0) c->w.input_err = (int32_t *)p;
+    if (!rc && cudaMemset(c->w.input_err, 0, sizeof(int32_t)) != cudaSuccess) rc = POLYLLA_ERR_CUDA;
+    // the union origin is filled by the layout check at create only; every
+    // generate writes the interior union twins from the local arrays
     c->mesh.origin = c->u_origin;
     c->mesh.twin = c->u_twin;
+    c->w.loc_origin = origin;
+    c->w.loc_twin = twin;
+    c->w.u_twin = c->u_twin;
     bv.v_off = d_off[0];
     bv.t_off = d_off[1];
     bv.h_off = d_off[2];
@@ -406,10 +413,11 @@ int polylla_create_host(polylla_ctx **out, int32_t n_vertices, int32_t n_triangl
 
 }  // extern "C"
 
-// Enqueue one whole run on s: for a batch, packing, then the method's
-// stages on the union (which also write each mesh's own next/prev, seeds
-// and polygon ranges), then, when serving, the per-mesh metadata; with
-// timing, an event pair around every stage.
+// Enqueue one whole run on s: the method's stages (on a batch, on its union:
+// the longest-edge kernel reads the meshes' own arrays and writes the union
+// twins, the later kernels also write each mesh's own next/prev, seeds and
+// polygon ranges), then, when serving, the per-mesh metadata; with timing,
+// an event pair around every stage.
 static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
     for (int i = 0; i < kStages; i++) c->stage_ran[i] = false;
     auto begin = [&](int i) -> cudaError_t {
@@ -417,12 +425,6 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
         return timing ? cudaEventRecord(c->ev_begin[i], s) : cudaSuccess;
     };
     auto end = [&](int i) -> cudaError_t { return timing ? cudaEventRecord(c->ev_end[i], s) : cudaSuccess; };
-    if (c->is_batch) {
-        CK(begin(kPack));
-        CK(cudaMemsetAsync(c->w.input_err, 0, sizeof(int32_t), s));
-        launch_batch_pack(c->bv, c->u_origin, c->u_twin, nullptr, nullptr, nullptr, c->w.input_err, s);
-        CK(end(kPack));
-    }
     void (*stages[kCore])(const MeshView &, const Work &, cudaStream_t) = {
         launch_longest_edge, launch_label_relink, launch_chords, launch_chord_links, launch_poly_count,
         launch_tile_scan, launch_poly_list,
@@ -441,7 +443,7 @@ static int enqueue(polylla_ctx *c, cudaStream_t s, bool timing) {
         if (c->serve) launch_batch_meta(c->bv, c->w, c->poly_off, c->local_offsets, c->meta, s);
         CK(end(kMeta));
     }
-    c->launches = kKernels + (c->is_batch ? kBatchKernels : 0) + (c->serve ? 1 : 0);
+    c->launches = kKernels + (c->serve ? 1 : 0);
     CK(cudaGetLastError());
     return POLYLLA_OK;
 }
@@ -678,6 +680,21 @@ int polylla_batch_create(polylla_ctx **out, const polylla_batch *b, const polyll
             for (int k = 0; k < 4 && e == cudaSuccess; k++)
                 e = cudaMemcpy(d_off[k], src[k], sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice);
             delete[] h_b;
+            // the mesh table: the mesh of every SEG_SPAN-th triangle
+            const int64_t ns = seg_count(to[n]);
+            int32_t *h_seg = e == cudaSuccess ? new (std::nothrow) int32_t[(size_t)ns] : nullptr;
+            if (e == cudaSuccess && !h_seg) rc = POLYLLA_ERR_OUT_OF_MEMORY;
+            if (h_seg) {
+                int32_t i = 0;
+                for (int64_t g = 0; g < ns; g++) {
+                    const int64_t t = std::min<int64_t>(g * SEG_SPAN, (int64_t)to[n] - 1);
+                    while (i + 1 < n && to[i + 1] <= t) i++;
+                    h_seg[g] = i;
+                }
+                e = cudaMemcpy(const_cast<int32_t *>(c->w.loc_seg), h_seg, sizeof(int32_t) * (size_t)ns,
+                               cudaMemcpyHostToDevice);
+                delete[] h_seg;
+            }
             if (e != cudaSuccess) rc = cuda_fail(c, e);
         }
     }
@@ -960,6 +977,7 @@ int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const 
     c->w.n_tile_max = (int32_t)(((int64_t)T + OUT_TILE_MIN - 1) / OUT_TILE_MIN);
     launch_serve_offsets(off4, n, const_cast<int32_t *>(c->bv.v_off), const_cast<int32_t *>(c->bv.t_off),
                          const_cast<int32_t *>(c->bv.h_off), const_cast<int32_t *>(c->bv.b_off), s);
+    launch_batch_seg(c->bv.t_off, n, T, const_cast<int32_t *>(c->w.loc_seg), s);
     c->last_stream = s;
     c->timed_last = false;
     return enqueue(c, s, false);

@@ -17,8 +17,10 @@
 //   poly_wtot [T/128+34] u64  per output warp: its (polygons, length) total
 //   seeds [T], offsets [T+1], he_list [3T], v_list [3T]   CSR output
 //   ctrl          DevCtrl       counters and the device error word
-// A batch context adds the union origin/twin/next/prev [H], the per-mesh
-// prefix sums and polygon ranges, and the input-check word.
+// A batch context adds the union origin/twin/next/prev [H] (origin and the
+// border entries of twin are only filled by the layout check at create; every
+// generate writes the interior twin entries from the meshes' own arrays), the
+// per-mesh prefix sums and polygon ranges, and the input-check word.
 #pragma once
 
 #include <cstdint>
@@ -31,7 +33,7 @@ enum : int32_t {
     DEV_ERR_NONTERMINATING = 1,
     DEV_ERR_CAPACITY = 2,
     DEV_ERR_TIMEOUT = 4,
-    DEV_ERR_INPUT = 8,           // a batch mesh held an index out of its range
+    DEV_ERR_INPUT = 8,           // a batch mesh held an index outside its own range
 };
 
 struct DevCtrl {
@@ -86,7 +88,12 @@ struct Work {
     int32_t *loc_prev;           //   by the relink and repair kernels
     int32_t *loc_poly_off;       // [loc_n+1] first polygon of each mesh, P at the end
     int32_t loc_n;               // number of meshes (0: a single mesh)
-    int32_t *input_err;          // batches: set by the pack on an out-of-range index
+    const int32_t *loc_seg;      // [T/256 + 1] mesh of triangle 256 g (SEG_SPAN)
+    const int32_t *loc_origin;   // the meshes' own origin and twin arrays (local indices),
+    const int32_t *loc_twin;     //   read by the longest-edge and listing kernels
+    int32_t *u_twin;             // union twin of interior half-edges, written by the longest-edge kernel
+    int32_t *input_err;          // batches: set on an index outside its mesh, folded into
+                                 //   the error word and cleared by the tile scan
 };
 
 // A batch of independent meshes, each in the single-mesh layout with its own
@@ -175,6 +182,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+// batches: the mesh table holds the mesh of every SEG_SPAN-th triangle
+constexpr int SEG_SPAN = 256;
+__host__ __device__ constexpr int64_t seg_count(int64_t T) { return T / SEG_SPAN + 1; }
+
 // largest i in [0, n) with off[i] <= x, for ascending prefix sums off[0..n]
 // with off[0] <= x < off[n]
 __device__ __forceinline__ int32_t seg_of(const int32_t *off, int32_t n, int32_t x) {
@@ -185,6 +196,14 @@ __device__ __forceinline__ int32_t seg_of(const int32_t *off, int32_t n, int32_t
         else hi = mid - 1;
     }
     return lo;
+}
+
+// the mesh of union triangle t of a batch: from the mesh table's entry at
+// or before t, stepping over the meshes that end by t
+__device__ __forceinline__ int32_t mesh_of(const int32_t *seg, const int32_t *t_off, int32_t n, int32_t t) {
+    int32_t j = __ldg(seg + t / SEG_SPAN);
+    while (j + 1 < n && __ldg(t_off + j + 1) <= t) j++;
+    return j;
 }
 
 // ---- float32 filters of float64 decisions -----------------------------------
@@ -260,6 +279,7 @@ void launch_lepp_paths(const MeshView &m, const Work &w, const int32_t *tri, int
 // batches (kernels_batch.cu)
 void launch_batch_pack(const BatchView &b, int32_t *u_origin, int32_t *u_twin, int32_t *u_next, int32_t *u_prev,
                        int32_t *bad, int32_t *input_err, cudaStream_t s);
+void launch_batch_seg(const int32_t *t_off, int32_t n, int32_t T, int32_t *seg, cudaStream_t s);
 void launch_batch_meta(const BatchView &b, const Work &w, const int32_t *poly_off, int32_t *local_offsets,
                        int32_t *meta, cudaStream_t s);
 

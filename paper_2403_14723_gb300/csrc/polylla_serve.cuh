@@ -21,7 +21,7 @@ size_t serve_bytes(const polylla_ctx *c);
 // Bind n meshes of V, T, H in total and enqueue the whole run on s: a
 // kernel copy of the prefix sums off4 = {v[n+1], t[n+1], h[n+1], b[n+1]}
 // (the device address of pinned host memory that must stay valid until the
-// run completes), packing, the method's stages and the per-mesh metadata.
+// run completes), the method's stages and the per-mesh metadata.
 int serve_run(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t H, const int32_t *off4, cudaStream_t s);
 
 // Device outputs of the last run (valid once it completes, until the next).

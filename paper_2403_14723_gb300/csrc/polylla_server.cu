@@ -6,7 +6,7 @@
 // order, as many waiting requests as fit the slot's capacity (meshes,
 // triangles, vertices, half-edges), copies their coords, origin and twin
 // into the slot's device arena (the method never reads next/prev), runs the
-// batch (pack, the method's stages, per-mesh metadata) and moves
+// batch (the method's stages, per-mesh metadata) and moves
 // the per-mesh metadata to pinned host memory.  When that has landed it
 // copies each request's CSR slices and interior next/prev back into the
 // request's host buffers (border entries are the input's, copied on the
@@ -49,12 +49,13 @@ using Clock = std::chrono::steady_clock;
 constexpr int kMaxCeSlots = 16;           // copy-engine slots
 constexpr int kMaxSlots = kMaxCeSlots + 1; // and the lane
 constexpr int64_t kLaneBatch = 16;        // the lane slot holds 16 requests of the lane's largest size
+constexpr int kGroups = 32;          // completion groups of a copy-engine batch
 constexpr size_t kLogKeep = 65536;  // completed batches kept for polylla_server_get_batch_log
 constexpr int32_t kLaneDefault = 65536;  // lane_triangles when the option is 0
 constexpr double kStealSeconds = 0.005;  // a lane request older than this may join any batch
-// kernels per batch; the run is 10 (pack 2, the method 7, metadata 1)
-constexpr int32_t kLaunchesCE = 12;      // per batch: offsets, the run, metadata out
-constexpr int32_t kLaunchesLane = 13;    // per lane batch: gather, offsets, the run, scatter
+// kernels per batch; the run is 8 (the method 7, metadata 1)
+constexpr int32_t kLaunchesCE = 11;      // per batch: offsets, mesh table, the run, metadata out
+constexpr int32_t kLaunchesLane = 12;    // per lane batch: gather, offsets, mesh table, the run, scatter
 
 struct Req {
     polylla_request r{};
@@ -84,6 +85,14 @@ struct Slot {
     int32_t *d_off = nullptr, *d_meta = nullptr;
     DevCtrl *d_ctrl = nullptr;
     ServeTab *d_tab = nullptr;
+    // copy-engine slots: one event after the result copies of each group of
+    // consecutive requests (one request per group up to kGroups requests),
+    // so a request completes when its own results have landed instead of
+    // when the whole batch's have
+    cudaEvent_t ev_grp[kGroups] = {};
+    int32_t grp_end[kGroups] = {};  // group g: requests [grp_end[g - 1], grp_end[g])
+    int32_t n_grp = 0, grp_done = 0;
+    int32_t n_done = 0;             // requests [0, n_done) of the batch completed
     bool lane = false;         // the low-latency lane (slot 0 when enabled)
     int32_t n_cap = 0, V_cap = 0, T_cap = 0, H_cap = 0;
     std::vector<Req *> reqs;
@@ -94,7 +103,7 @@ struct Slot {
 // metadata), following the allocations of serve_reserve and the arena.
 int64_t slot_bytes(int64_t n, int64_t V, int64_t T, int64_t H) {
     const int64_t arena = 16 * V + 16 * H;
-    const int64_t uni = 16 * H + 20 * (n + 1);
+    const int64_t uni = 16 * H + 20 * (n + 1) + 4 * seg_count(T);
     const int64_t meta = 16 * n + 4 * (T + n + 1);
     const int64_t Tpad = (T + 15) / 16 * 16;
     const int64_t work = 2 * Tpad + 8 * V + 16 * ((T + OUT_TILE_MIN - 1) / OUT_TILE_MIN) + 16 * ((T + OUT_TILE_MIN - 1) / OUT_TILE_MIN / 1024 + 1) + 8 * out_rec_count(T) + 8 * out_warp_count(T) +
@@ -189,8 +198,9 @@ void polylla_server::complete(Req *q, int status) {
 }
 
 void polylla_server::finish(Slot &s, int status) {
-    for (Req *q : s.reqs) complete(q, status);
+    for (size_t i = (size_t)s.n_done; i < s.reqs.size(); i++) complete(s.reqs[i], status);
     s.reqs.clear();
+    s.n_done = s.n_grp = s.grp_done = 0;
     s.state = 0;
 }
 
@@ -233,6 +243,7 @@ bool polylla_server::launch(Slot &s) {
     s.rec.n_requests = n;
     s.rec.n_triangles = to[n];
     s.reqs = take;
+    s.n_done = s.n_grp = s.grp_done = 0;
     for (Req *q : take) {
         q->t_admit = t;
         q->batch_meshes = n;
@@ -321,6 +332,9 @@ void polylla_server::copy_out(Slot &s) {
     serve_outputs(s.ctx, &o);
     const int32_t n = (int32_t)s.reqs.size();
     const int32_t *ho = s.h_off + 2 * (n + 1);
+    const int32_t G = std::min(n, kGroups);
+    for (int32_t g = 0; g < G; g++) s.grp_end[g] = (int32_t)(((int64_t)(g + 1) * n) / G);
+    int32_t g = 0;
     cudaError_t e = cudaEventRecord(s.ev_o0, s.stream);
     for (int32_t i = 0; i < n && e == cudaSuccess; i++) {
         Req *q = s.reqs[i];
@@ -344,7 +358,9 @@ void polylla_server::copy_out(Slot &s) {
             memcpy(out.next + n_int, q->r.mesh.next + n_int, Hb - HIb);
             memcpy(out.prev + n_int, q->r.mesh.prev + n_int, Hb - HIb);
         }
+        if (e == cudaSuccess && i + 1 == s.grp_end[g]) e = cudaEventRecord(s.ev_grp[g++], s.stream);
     }
+    s.n_grp = e == cudaSuccess ? G : 0;
     if (e == cudaSuccess) e = cudaEventRecord(s.ev_out, s.stream);
     if (e == cudaSuccess) e = cudaEventRecord(s.ev_to, s.stream);
     s.rec.t_out_enqueued = now();
@@ -372,6 +388,19 @@ void polylla_server::loop() {
                     progressed = true;
                 } else if (q != cudaErrorNotReady) {
                     finish(s, POLYLLA_ERR_CUDA);
+                    progressed = true;
+                }
+            }
+            if (s.state == 2 && !s.lane) {
+                // requests whose own results have landed complete now
+                while (s.grp_done < s.n_grp && cudaEventQuery(s.ev_grp[s.grp_done]) == cudaSuccess) {
+                    const int32_t end = s.grp_end[s.grp_done++];
+                    for (; s.n_done < end; s.n_done++) {
+                        Req *r = s.reqs[(size_t)s.n_done];
+                        r->r.result.n_polygons = r->P;
+                        r->r.result.n_frontier = r->NF;
+                        complete(r, POLYLLA_OK);
+                    }
                     progressed = true;
                 }
             }
@@ -427,7 +456,8 @@ void polylla_server::loop() {
                         s.reqs.clear();
                         s.state = 0;
                     } else {
-                        for (Req *r : s.reqs) {
+                        for (size_t i = (size_t)s.n_done; i < s.reqs.size(); i++) {
+                            Req *r = s.reqs[i];
                             r->r.result.n_polygons = r->P;
                             r->r.result.n_frontier = r->NF;
                         }
@@ -480,6 +510,8 @@ static void free_slot(Slot &s) {
     for (cudaEvent_t ev : {s.ev_t0, s.ev_in, s.ev_tm, s.ev_o0, s.ev_to})
         if (ev) cudaEventDestroy(ev);
     if (s.ev_out) cudaEventDestroy(s.ev_out);
+    for (cudaEvent_t ev : s.ev_grp)
+        if (ev) cudaEventDestroy(ev);
     if (s.stream) cudaStreamDestroy(s.stream);
     s = Slot();
 }
@@ -541,6 +573,8 @@ static int make_slot(polylla_server *srv, Slot &s, int32_t n, int32_t V, int32_t
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_tm);
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_o0);
     if (e == cudaSuccess) e = cudaEventCreate(&s.ev_to);
+    for (int g = 0; g < kGroups && e == cudaSuccess && !lane; g++)
+        e = cudaEventCreateWithFlags(&s.ev_grp[g], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.coords, 16 * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.origin, 4 * (size_t)H);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.twin, 4 * (size_t)H);

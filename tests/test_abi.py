@@ -49,10 +49,11 @@ def test_status_strings_without_gpu(lib_path):
     lib = polylla.load_library()
     assert lib.polylla_status_string(0) == b"ok"
     assert lib.polylla_status_string(-2) == b"invalid mesh layout"
-    assert lib.polylla_stage_count() == 9
-    names = [lib.polylla_stage_name(i).decode() for i in range(9)]
+    assert lib.polylla_stage_count() == 8
+    names = [lib.polylla_stage_name(i).decode() for i in range(8)]
+    assert lib.polylla_stage_name(8) == b""
     assert names == ["longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan",
-                     "poly_list", "batch_pack", "batch_meta"]
+                     "poly_list", "batch_meta"]
 
 
 def test_null_arguments_rejected_without_gpu(lib_path):

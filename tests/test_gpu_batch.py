@@ -94,7 +94,7 @@ def assert_batch_parity(meshes, db, g):
 def test_batch_matches_oracle_per_mesh():
     meshes = _mix()
     db, g = batch_run(meshes)
-    assert g["launches"] == 9
+    assert g["launches"] == 7
     assert_batch_parity(meshes, db, g)
 
 

@@ -203,7 +203,7 @@ def test_stage_timing_and_launch_count():
         p.generate()
         t = polylla.polylla_get_stage_times(p.ctx)
         assert list(t) == ["longest_edge", "label_relink", "chords", "chord_links", "poly_count", "tile_scan",
-                           "poly_list", "batch_pack", "batch_meta"]
+                           "poly_list", "batch_meta"]
         assert all(v >= 0 for v in t.values())
-        assert t["batch_pack"] == 0 and t["batch_meta"] == 0
+        assert t["batch_meta"] == 0
         assert polylla.polylla_launch_count(p.ctx) == 7

@@ -75,7 +75,7 @@ def test_served_requests_match_oracle_alone_and_in_the_mix():
         for k in ("n_slots", "slot_triangles", "lane_triangles", "lane_slot_triangles"):
             assert st[k] == plan[k], k
         assert any(b["lane"] == 1 for b in log) and any(b["lane"] == 0 for b in log)
-        assert st["launches"] == 13 * st["lane_batches"] + 12 * (st["batches"] - st["lane_batches"])
+        assert st["launches"] == 12 * st["lane_batches"] + 11 * (st["batches"] - st["lane_batches"])
 
 
 def test_copy_paths_give_identical_results():
@@ -160,9 +160,9 @@ def test_served_recipe_pool_matches_oracle():
 
 
 def test_malformed_request_fails_cleanly():
-    """Indices outside a request's own mesh are caught by the packing, kept
-    inside the mesh (no access leaves it) and reported as an invalid mesh;
-    the server keeps serving."""
+    """Indices outside a request's own mesh are caught by the longest-edge
+    kernel's range checks, kept inside the mesh (no access leaves it) and
+    reported as an invalid mesh; the server keeps serving."""
     build.build_library()
     good = meshgen.random_delaunay(300, seed=12)
     bad = meshgen.random_delaunay(300, seed=13)
