@@ -234,78 +234,129 @@ __global__ void __launch_bounds__(LE_THREADS) k_longest_edge(MeshView m, Work w)
 
 // ===========================================================================
 // Stage 1 on a batch, straight from the meshes' own arrays (no packing
-// pass).  One thread per triangle of the union; each thread finds its
-// mesh from the batch's mesh table (the mesh of every 256th triangle) and
-// steps forward over the meshes that end before its triangle.  The
-// local half-edge 3 (t - t_off) + k of triangle t of mesh j sits at
-// h_off + 3 (t - t_off) + k in the concatenated local arrays.  Every origin
-// and twin is range-checked against its mesh: an index outside it is
-// replaced by one inside it (vertex 0; the mesh's first border half-edge,
-// which stops rotations) and the run is flagged, so no later kernel reads
-// outside the mesh.  The thread writes its three half-edges' union twins
-// (interior: 3 t_off + y; border: 3 T + b_off + (y - 3 T_j)), which the
-// later stages walk, and the longest edge as on a single mesh, from the
-// coordinates at the mesh's vertex offset.
+// pass).  Persistent warps with a two-stage ring as in k_longest_edge; a
+// warp's tile of 32 PER triangles that lies inside one mesh has its origin
+// and twin entries contiguous in the mesh's local arrays (local half-edge
+// 3 (t - t_off) + k of triangle t of mesh j sits at h_off + 3 (t - t_off)
+// + k), so lane 0 bulk-copies both from that start rounded down to 16
+// bytes (r entries early) to 16 bytes past the end, which stays inside the
+// mesh's entries since at least 3 border half-edges follow its interior
+// ones.  A tile across meshes, or arrays that do not start on a 16-byte
+// boundary, are read with plain loads.  The mesh comes from the batch's
+// mesh table (the mesh of every 256th triangle).  Every origin and twin is
+// range-checked against its mesh: an index outside it is replaced by one
+// inside it (vertex 0; the mesh's first border half-edge, which stops
+// rotations) and the run is flagged, so no later kernel reads outside the
+// mesh.  Each lane writes its triangles' union twins (interior: 3 t_off +
+// y; border: 3 T + b_off + (y - 3 T_j)), which the later stages walk, and
+// the longest edge as on a single mesh, from the coordinates at the mesh's
+// vertex offset.
 // ===========================================================================
-constexpr int LEB_THREADS = 256;
-constexpr int LEB_ITEMS = 2;  // triangles per thread, their loads in flight together
-
-__global__ void __launch_bounds__(LEB_THREADS) k_longest_edge_batch(MeshView m, Work w) {
+template <int PER>
+__global__ void __launch_bounds__(LE_THREADS) k_longest_edge_batch(MeshView m, Work w) {
+    constexpr int NW = LE_THREADS / 32;
+    constexpr int LE_TILE = 32 * PER;
+    constexpr int SPAN = 3 * LE_TILE + 4;  // a stage's entries, 4 to spare for an unaligned start
+    static_assert(SPAN % 4 == 0, "stages start on 16-byte boundaries");
+    __shared__ __align__(128) int32_t s_org[NW][2][SPAN];
+    __shared__ __align__(128) int32_t s_tw[NW][2][SPAN];
+    __shared__ __align__(8) uint64_t s_bar[NW][2];
+    __shared__ int32_t s_r[NW][2], s_j[NW][2];  // per stage: start offset (-1: plain loads), mesh
     const int32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gtid < (int32_t)(sizeof(DevCtrl) / sizeof(int32_t))) reinterpret_cast<int32_t *>(w.ctrl)[gtid] = 0;
     for (int32_t i = gtid; i < w.n_tile_max; i += gridDim.x * blockDim.x) w.tile_state[i] = 0ull;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t HI = 3 * m.T;
-    const int32_t base = blockIdx.x * (LEB_THREADS * LEB_ITEMS) + (int32_t)threadIdx.x;
-    // per triangle: its mesh's constants, then all loads of origin and twin,
-    // then the checks and union twins, then all coordinate loads
-    int32_t g[LEB_ITEMS], t3[LEB_ITEMS], ti3[LEB_ITEMS], hi[LEB_ITEMS], vi[LEB_ITEMS], v0[LEB_ITEMS];
-#pragma unroll
-    for (int q = 0; q < LEB_ITEMS; q++) {
-        const int32_t t = base + q * LEB_THREADS;
-        g[q] = -1;
-        if (t < m.T) {
-            const int32_t j = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t);
-            t3[q] = 3 * __ldg(w.loc_t_off + j);
-            ti3[q] = 3 * __ldg(w.loc_t_off + j + 1) - t3[q];
-            const int32_t h0 = __ldg(w.loc_h_off + j);
-            hi[q] = __ldg(w.loc_h_off + j + 1) - h0;
-            v0[q] = __ldg(w.loc_v_off + j);
-            vi[q] = __ldg(w.loc_v_off + j + 1) - v0[q];
-            g[q] = h0 + (3 * t - t3[q]);
-        }
+    const int32_t n_tiles = (m.T + LE_TILE - 1) / LE_TILE;
+    uint64_t *bar = s_bar[warp];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
     }
-    int32_t o[LEB_ITEMS][3], tw[LEB_ITEMS][3];
-#pragma unroll
-    for (int q = 0; q < LEB_ITEMS; q++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            o[q][k] = g[q] >= 0 ? __ldg(w.loc_origin + g[q] + k) : 0;
-            tw[q][k] = g[q] >= 0 ? __ldg(w.loc_twin + g[q] + k) : 0;
+    __syncwarp();
+    auto issue = [&](int32_t tile, int st) {
+        const int32_t t0 = tile * LE_TILE;
+        const int32_t nt = min(LE_TILE, m.T - t0);
+        const int32_t j = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t0);
+        const int32_t t3 = 3 * __ldg(w.loc_t_off + j);
+        const bool one = w.loc_aligned && 3 * __ldg(w.loc_t_off + j + 1) >= 3 * (t0 + nt);
+        s_j[warp][st] = j;
+        fence_proxy_async_smem();
+        if (one) {
+            const int32_t L0 = __ldg(w.loc_h_off + j) + (3 * t0 - t3);
+            const int32_t r = L0 & 3;
+            const uint32_t bytes = ((uint32_t)(r + 3 * nt) * 4u + 15u) & ~15u;
+            s_r[warp][st] = r;
+            mbar_arrive_expect_tx(&bar[st], 2 * bytes);
+            bulk_load(s_org[warp][st], w.loc_origin + (L0 - r), bytes, &bar[st]);
+            bulk_load(s_tw[warp][st], w.loc_twin + (L0 - r), bytes, &bar[st]);
+        } else {
+            s_r[warp][st] = -1;
+            mbar_arrive_expect_tx(&bar[st], 0u);  // nothing to copy: the phase completes now
         }
+    };
+    const int32_t nwarps = gridDim.x * NW;
+    int32_t tile = blockIdx.x * NW + warp;
+    if (lane == 0 && tile < n_tiles) issue(tile, 0);
+    uint32_t parity = 0u;
     bool bad = false;
-    double2 p[LEB_ITEMS][3];
-#pragma unroll
-    for (int q = 0; q < LEB_ITEMS; q++) {
-        if (g[q] < 0) continue;
-        const int32_t e0 = 3 * (base + q * LEB_THREADS);
-        const int32_t bo = HI + (g[q] - (e0 - t3[q])) - t3[q] - ti3[q];  // HI + b_off - 3 T_j
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            if ((uint32_t)o[q][k] >= (uint32_t)vi[q]) { o[q][k] = 0; bad = true; }
-            if ((uint32_t)tw[q][k] >= (uint32_t)hi[q]) { tw[q][k] = ti3[q]; bad = true; }
-            tw[q][k] = tw[q][k] < ti3[q] ? t3[q] + tw[q][k] : bo + tw[q][k];
-            w.u_twin[e0 + k] = tw[q][k];
-            p[q][k] = __ldg(m.xy + v0[q] + o[q][k]);
+    for (int it = 0; tile < n_tiles; it++, tile += nwarps) {
+        const int st = it & 1;
+        const int32_t nxt = tile + nwarps;
+        if (lane == 0 && nxt < n_tiles) issue(nxt, st ^ 1);
+        const bool ok = mbar_wait(&bar[st], (parity >> st) & 1u);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) atomicOr(&w.ctrl->error, DEV_ERR_TIMEOUT);
+            mbar_wait(&bar[st], (parity >> st) & 1u);
+            if (nxt < n_tiles) mbar_wait(&bar[st ^ 1], (parity >> (st ^ 1)) & 1u);
+            return;
         }
+        parity ^= 1u << st;
+        const int32_t t0 = tile * LE_TILE;
+        const int32_t r = s_r[warp][st];
+        const int32_t *so = s_org[warp][st] + (r > 0 ? r : 0);
+        const int32_t *stw = s_tw[warp][st] + (r > 0 ? r : 0);
+        double2 p[PER][3];
+        int32_t tw[PER][3];
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int32_t lt = lane + 32 * q;
+            const int32_t t = t0 + lt;
+            if (t >= m.T) continue;
+            const int32_t j = r >= 0 ? s_j[warp][st] : mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t);
+            const int32_t t3 = 3 * __ldg(w.loc_t_off + j);
+            const int32_t ti3 = 3 * __ldg(w.loc_t_off + j + 1) - t3;
+            const int32_t h0 = __ldg(w.loc_h_off + j), hi = __ldg(w.loc_h_off + j + 1) - h0;
+            const int32_t v0 = __ldg(w.loc_v_off + j), vi = __ldg(w.loc_v_off + j + 1) - v0;
+            const int32_t g = h0 + (3 * t - t3);
+            const int32_t bo = HI + (h0 - t3) - ti3;
+            int32_t o[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                o[k] = r >= 0 ? so[3 * lt + k] : __ldg(w.loc_origin + g + k);
+                tw[q][k] = r >= 0 ? stw[3 * lt + k] : __ldg(w.loc_twin + g + k);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if ((uint32_t)o[k] >= (uint32_t)vi) { o[k] = 0; bad = true; }
+                if ((uint32_t)tw[q][k] >= (uint32_t)hi) { tw[q][k] = ti3; bad = true; }
+                tw[q][k] = tw[q][k] < ti3 ? t3 + tw[q][k] : bo + tw[q][k];
+                w.u_twin[3 * t + k] = tw[q][k];
+                p[q][k] = __ldg(m.xy + v0 + o[k]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int32_t t = t0 + lane + 32 * q;
+            const int32_t *twq = tw[q];
+            if (t < m.T)
+                w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t, [twq](int k) { return twq[k]; });
+        }
+        __syncwarp();  // stage st is refilled next iteration
     }
     if (bad) atomicOr(w.input_err, 1);
-#pragma unroll
-    for (int q = 0; q < LEB_ITEMS; q++) {
-        if (g[q] < 0) continue;
-        const int32_t t = base + q * LEB_THREADS;
-        const int32_t *twq = tw[q];
-        w.le[t] = (uint8_t)longest_of(p[q][0], p[q][1], p[q][2], 3 * t, [twq](int k) { return twq[k]; });
-    }
 }
 
 int longest_edge_blocks_per_sm(int32_t items) {
@@ -317,18 +368,21 @@ int longest_edge_blocks_per_sm(int32_t items) {
     return n > 0 ? n : 1;
 }
 
+int longest_edge_batch_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_longest_edge_batch<2>, LE_THREADS, 0) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
+
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s) {
-    if (w.loc_n > 0) {
-        const int32_t span = LEB_THREADS * LEB_ITEMS;
-        k_longest_edge_batch<<<(m.T + span - 1) / span, LEB_THREADS, 0, s>>>(m, w);
-        return;
-    }
-    const int32_t tile = 32 * (w.le_items == 4 ? 4 : 2);
+    const int32_t tile = 32 * (w.le_items == 4 && w.loc_n == 0 ? 4 : 2);  // batches: 2 per lane
     const int32_t n_tiles = (m.T + tile - 1) / tile;
     const int32_t want = (n_tiles + LE_THREADS / 32 - 1) / (LE_THREADS / 32);  // one tile per warp
-    const int blocks = want < w.le_blocks ? want : w.le_blocks;
+    const int32_t grid = w.loc_n > 0 ? w.le_batch_blocks : w.le_blocks;  // persistent: every CTA resident
+    const int blocks = want < grid ? want : grid;
     // the control-block reset needs >= 8 threads: any grid >= 1 works
-    if (w.le_items == 4) k_longest_edge<4><<<blocks, LE_THREADS, 0, s>>>(m, w);
+    if (w.loc_n > 0) k_longest_edge_batch<2><<<blocks, LE_THREADS, 0, s>>>(m, w);
+    else if (w.le_items == 4) k_longest_edge<4><<<blocks, LE_THREADS, 0, s>>>(m, w);
     else k_longest_edge<2><<<blocks, LE_THREADS, 0, s>>>(m, w);
 }
 

@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     constexpr int WCAP = 64 * IPT;  // CSR entries a warp stages
     extern __shared__ __align__(128) unsigned char smem[];
     int32_t *s_nx = reinterpret_cast<int32_t *>(smem);  // [E]
-    int32_t *s_org = s_nx + E;                          // [E]
-    int32_t *s_stage = s_org + E;                       // [NW][2][WCAP]
+    int32_t *s_org = s_nx + E;                          // [E + 4]
+    int32_t *s_stage = s_org + E + 4;                   // [NW][2][WCAP]
     __shared__ __align__(8) uint64_t s_bar;
     const int32_t HI = 3 * m.T;
     const int32_t tile = blockIdx.x;
@@ -291,19 +291,39 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
     const int32_t eb = 3 * t0;
     const uint32_t ne = (uint32_t)(3 * nt);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int32_t s_j0;  // batches: the mesh of the tile's first triangle
+    // batches: the mesh of the tile's first triangle, and where the tile's
+    // origins start in s_org (-1: not bulk-copied, loaded below)
+    __shared__ int32_t s_j0, s_r;
     if (threadIdx.x == 0) {
         mbar_init(&s_bar, 1);
         fence_mbar_init();
         const uint32_t be = tile_bytes(nt, 12);
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&s_bar, BATCH ? be : 2 * be);
-        bulk_load(s_nx, m.next + eb, be, &s_bar);
-        if (!BATCH) bulk_load(s_org, m.origin + eb, be, &s_bar);
-        else s_j0 = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t0);
+        if (!BATCH) {
+            mbar_arrive_expect_tx(&s_bar, 2 * be);
+            bulk_load(s_nx, m.next + eb, be, &s_bar);
+            bulk_load(s_org, m.origin + eb, be, &s_bar);
+            s_r = 0;
+        } else {
+            // a tile inside one mesh has its origins contiguous in the local
+            // array, from entry L0: bulk-copy from L0 rounded down to 16 bytes
+            // (r entries early) to 16 bytes past the end, which stays inside
+            // the mesh's entries since at least 3 border half-edges follow
+            // its interior ones
+            const int32_t j = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t0);
+            s_j0 = j;
+            const bool one = w.loc_aligned && 3 * __ldg(w.loc_t_off + j + 1) >= eb + (int32_t)ne;
+            const int32_t L0 = eb + __ldg(w.loc_h_off + j) - 3 * __ldg(w.loc_t_off + j);
+            const int32_t r = L0 & 3;
+            const uint32_t bo = ((uint32_t)(r + (int32_t)ne) * 4u + 15u) & ~15u;
+            mbar_arrive_expect_tx(&s_bar, one ? be + bo : be);
+            bulk_load(s_nx, m.next + eb, be, &s_bar);
+            if (one) bulk_load(s_org, w.loc_origin + (L0 - r), bo, &s_bar);
+            s_r = one ? r : -1;
+        }
     }
     __syncthreads();
-    if (BATCH) {
+    if (BATCH && s_r < 0) {
         // origin from the meshes' own arrays (already local vertex ids): union
         // half-edge x of mesh j is local entry x + h_off[j] - 3 t_off[j].  All
         // of a thread's addresses first, then all its loads, then the stores,
@@ -337,6 +357,7 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
         }
         __syncthreads();
     }
+    const int32_t *so = s_org + (s_r > 0 ? s_r : 0);  // the tile's origins
     const int64_t rec = (int64_t)tile * NT + threadIdx.x;
     const unsigned long long r = w.poly_rec[rec];
     const unsigned long long ex = ((r >> REC_CNT_SHIFT) & REC_CNT_MASK) << 32 | (r & REC_LEN_MASK);
@@ -410,7 +431,7 @@ __global__ void __launch_bounds__(NT) k_poly_list(MeshView m, Work w) {
         do {  // k_poly_count's walk came back to e: this loop ends
             const uint32_t d = (uint32_t)(x - eb);
             const bool in = d < ne;
-            const int32_t v = in ? s_org[d] : BATCH ? __ldg(w.loc_origin + x + sb) : __ldg(m.origin + x);
+            const int32_t v = in ? so[d] : BATCH ? __ldg(w.loc_origin + x + sb) : __ldg(m.origin + x);
             if (pos < WCAP) {
                 st_he[pos] = x - she;
                 st_v[pos] = v;
@@ -437,9 +458,10 @@ constexpr size_t count_smem() {
 }
 template <int TILE>
 constexpr size_t list_smem() {
-    // next and origin of the tile, and per warp 2 x 64 x (TILE / NT) staged
-    // entries: 4 TILE ints in all
-    return (size_t)(2 * 3 * TILE + 4 * TILE) * sizeof(int32_t);
+    // next and origin of the tile (origin with 4 entries to spare for an
+    // unaligned start), and per warp 2 x 64 x (TILE / NT) staged entries:
+    // 4 TILE ints in all
+    return (size_t)(2 * 3 * TILE + 4 + 4 * TILE) * sizeof(int32_t);
 }
 
 #define POLYGON_CONFIGS(X) \

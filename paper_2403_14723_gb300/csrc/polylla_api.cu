@@ -253,6 +253,7 @@ static int alloc_work(polylla_ctx *c, const polylla_options *opt) {
     c->w.persistent_blocks = 4 * (sms > 0 ? sms : 1);
     c->w.le_items = LE_ITEMS_DEFAULT;
     c->w.le_blocks = longest_edge_blocks_per_sm(LE_ITEMS_DEFAULT) * (sms > 0 ? sms : 1);
+    c->w.le_batch_blocks = longest_edge_batch_blocks_per_sm() * (sms > 0 ? sms : 1);
     c->w.out_tile = OUT_TILE_DEFAULT;
     c->w.out_items = OUT_ITEMS_DEFAULT;
     c->w.rl_tile = RL_TILE_DEFAULT;
@@ -304,6 +305,7 @@ static int batch_alloc(polylla_ctx *c, int32_t n, int32_t V, int32_t T, int32_t 
     c->mesh.origin = c->u_origin;
     c->mesh.twin = c->u_twin;
     c->w.loc_origin = origin;
+    c->w.loc_aligned = ((uintptr_t)origin & 15u) == 0 && ((uintptr_t)twin & 15u) == 0;
     c->w.loc_twin = twin;
     c->w.u_twin = c->u_twin;
     bv.v_off = d_off[0];

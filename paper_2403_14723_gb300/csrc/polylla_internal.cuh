@@ -80,6 +80,7 @@ struct Work {
     int32_t persistent_blocks;   // grid of the sparse (tip) kernels
     int32_t le_blocks;           // grid of the persistent longest-edge kernel
     int32_t le_items;            // longest edge: triangles per lane (2 or 4)
+    int32_t le_batch_blocks;     // grid of the persistent longest-edge kernel on batches
     // batches: the emitted he_list / v_list are made mesh-local when set
     const int32_t *loc_t_off;    // [loc_n+1] triangle offset of each mesh
     const int32_t *loc_v_off;    // [loc_n+1] vertex offset of each mesh
@@ -89,6 +90,7 @@ struct Work {
     int32_t *loc_poly_off;       // [loc_n+1] first polygon of each mesh, P at the end
     int32_t loc_n;               // number of meshes (0: a single mesh)
     const int32_t *loc_seg;      // [T/256 + 1] mesh of triangle 256 g (SEG_SPAN)
+    int32_t loc_aligned;         // loc_origin and loc_twin start on 16-byte boundaries (bulk copies allowed)
     const int32_t *loc_origin;   // the meshes' own origin and twin arrays (local indices),
     const int32_t *loc_twin;     //   read by the longest-edge and listing kernels
     int32_t *u_twin;             // union twin of interior half-edges, written by the longest-edge kernel
@@ -243,6 +245,7 @@ __device__ __forceinline__ int32_t pv_of(int32_t e) {
 void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s);
 void launch_longest_edge(const MeshView &m, const Work &w, cudaStream_t s);
 int longest_edge_blocks_per_sm(int32_t items);
+int longest_edge_batch_blocks_per_sm();
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s);
 // allows the relink kernels their shared memory on the current device (once
 // per device before the first launch); 0 on success

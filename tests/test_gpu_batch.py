@@ -39,11 +39,20 @@ def _mix():
     return ms
 
 
-def batch_run(meshes, graph=False, tune=False, generate_times=1):
+def batch_run(meshes, graph=False, tune=False, generate_times=1, unaligned=False):
     import torch
 
     build.build_library()
     db = polylla.DeviceBatch.from_host(meshes)
+    if unaligned:
+        # origin and twin one entry past a 16-byte boundary: the listing kernel
+        # cannot bulk-copy a tile's local origins and loads them one by one
+        for name in ("origin", "twin"):
+            a = getattr(db, name)
+            buf = torch.empty(a.numel() + 1, dtype=a.dtype, device=a.device)
+            buf[1:].copy_(a)
+            setattr(db, name, buf[1:])
+            assert getattr(db, name).data_ptr() % 16 == 4
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = polylla.polylla_batch_create(db, stream=stream)
@@ -95,6 +104,12 @@ def test_batch_matches_oracle_per_mesh():
     meshes = _mix()
     db, g = batch_run(meshes)
     assert g["launches"] == 7
+    assert_batch_parity(meshes, db, g)
+
+
+def test_batch_with_unaligned_local_arrays():
+    meshes = _mix()
+    db, g = batch_run(meshes, unaligned=True)
     assert_batch_parity(meshes, db, g)
 
 
