@@ -562,7 +562,8 @@ void polylla_server_destroy(polylla_server *srv);
  * thread, otherwise POLYLLA_OK or POLYLLA_ERR_CUDA.
  *
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) and sets the kernels' shared-memory limits.
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory limits; make
+ * that first call before any stream capture begins.
  * Every call shares the one array and it keeps the last call's contents:
  * calls that overlap on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.

@@ -609,15 +609,178 @@ __global__ void __launch_bounds__(NT, 2048 / NT / IPT) k_label_relink(MeshView m
     }
 }
 
-// launch configurations: (triangles per CTA, triangles per thread)
+// ===========================================================================
+// Stages 2-4 fused, one triangle per thread (the same labels, seeds, links,
+// tips and marks as k_label_relink).  A triangle's frontier half-edges form
+// at most one cyclic run among its three (one run, or none, or all three),
+// and only the last half-edge of a run has a successor across a
+// non-frontier edge: a triangle has at most one rotation.  With one
+// triangle per thread, each thread runs its own rotation: a warp's lanes
+// run their rotations side by side without any task list, and every next
+// entry of the CTA is set by its own thread.  prev goes through shared
+// memory (a rotation sets prev[x] for an x of another thread), which also
+// gives the walk-start marks their prev; each warp then stores the next and
+// prev of its 32 triangles as contiguous, coalesced runs.
+// ===========================================================================
+template <int NT, bool BATCH>
+__global__ void __launch_bounds__(NT, 2048 / NT) k_label_relink1(MeshView m, Work w) {
+    static_assert(NT % 32 == 0, "whole warps");
+    __shared__ int32_t s_pv[3 * NT];
+    __shared__ int32_t s_nx[3 * NT];
+    __shared__ int32_t s_m0;  // batches: the mesh of the CTA's first triangle
+    const int32_t t0 = blockIdx.x * NT;
+    const int32_t eb = 3 * t0;
+    const int32_t nE = 3 * min(NT, m.T - t0);
+    const int32_t HI = 3 * m.T;
+    const int32_t lb = 3 * (int32_t)threadIdx.x;
+    const int32_t t = t0 + (int32_t)threadIdx.x;
+    const bool live = t < m.T;
+    const int32_t e0 = 3 * t;
+    if (BATCH && threadIdx.x == 0) s_m0 = mesh_of(w.loc_seg, w.loc_t_off, w.loc_n, t0);
+    uint32_t F = 0, fl = 0;
+    uint32_t kt = 3;          // the local index of the rotating half-edge (3: none)
+    int32_t twk = 0;          // its twin (the rotation coming back to it finds a tip)
+    int32_t ty = 0;           // the rotation: current half-edge 3 ty + lx, ley = le(ty)
+    uint32_t lx = 0, ley = 0;
+    if (live) {
+        int32_t tw[3], ttri[3];
+        uint32_t tloc[3], lnb[3];
+        tw[0] = __ldg(m.twin + e0);
+        tw[1] = __ldg(m.twin + e0 + 1);
+        tw[2] = __ldg(m.twin + e0 + 2);
+        const uint32_t ltl = w.le[t];
+        uint32_t twle = 0;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const bool b = tw[k] >= HI;
+            ttri[k] = b ? 0 : div3(tw[k]);
+            tloc[k] = (uint32_t)(tw[k] - 3 * ttri[k]);
+            lnb[k] = b ? 3u : (uint32_t)w.le[ttri[k]];
+            const bool tl = !b && lnb[k] == tloc[k];
+            F |= (uint32_t)(b || ((uint32_t)k != ltl && !tl)) << k;
+            twle |= (uint32_t)tl << k;
+        }
+        const int32_t twl = ltl == 0u ? tw[0] : (ltl == 1u ? tw[1] : tw[2]);
+        const bool seed = (twl >= HI) || (((twle >> ltl) & 1u) && (e0 + (int32_t)ltl) < twl);
+        fl = F | ((uint32_t)seed << 6);
+        // prev of slot j: its triangle link when j is not frontier or its
+        // predecessor in the triangle is frontier; else set by a rotation
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const int k = j == 0 ? 2 : j - 1;
+            s_pv[lb + j] = (!((F >> j) & 1u) || ((F >> k) & 1u)) ? e0 + k : -1;
+        }
+        // the frontier half-edge whose successor in the triangle is not
+        // frontier: bit k of rot is F bit k + 1 (mod 3), so pend has one bit
+        // at most (1, 2 or 4 -> k = pend >> 1)
+        const uint32_t rot = ((F >> 1) | (F << 2)) & 7u;
+        const uint32_t pend = F & ~rot;
+        if (pend) {
+            kt = pend >> 1;
+            const uint32_t j = kt == 2u ? 0u : kt + 1u;
+            twk = kt == 0u ? tw[0] : (kt == 1u ? tw[1] : tw[2]);
+            ty = j == 0u ? ttri[0] : (j == 1u ? ttri[1] : ttri[2]);
+            const uint32_t ly = j == 0u ? tloc[0] : (j == 1u ? tloc[1] : tloc[2]);
+            ley = j == 0u ? lnb[0] : (j == 1u ? lnb[1] : lnb[2]);
+            lx = ly == 2u ? 0u : ly + 1u;
+        }
+    }
+    __syncthreads();  // every prev slot initialised before rotations write them
+    int32_t mj = 0, sh = 0;  // batches: the thread's mesh and its first union half-edge
+    if (BATCH && live) {
+        mj = s_m0;
+        while (mj + 1 < w.loc_n && __ldg(w.loc_t_off + mj + 1) <= t) mj++;
+        sh = 3 * __ldg(w.loc_t_off + mj);
+    }
+    int32_t x = 3 * ty + (int32_t)lx;
+    if (kt < 3u) {
+        // x = CW(next e) = next(twin(next e)); while x is not frontier,
+        // x = CW(x).  The next step's twin is fetched with this step's label.
+        const int32_t e = e0 + (int32_t)kt;
+        int32_t tx = __ldg(m.twin + x);
+        int32_t steps = 0;
+        while (true) {
+            if (tx >= HI) break;                     // border edge: frontier
+            const int32_t ttx = div3(tx);
+            const uint32_t ltx = (uint32_t)(tx - 3 * ttx);
+            const uint32_t lxn = ltx == 2u ? 0u : ltx + 1u;
+            const int32_t xn = 3 * ttx + (int32_t)lxn;
+            const uint32_t lex = w.le[ttx];
+            const int32_t txn = __ldg(m.twin + xn);
+            if (ley != lx && lex != ltx) break;      // neither half longest: frontier
+            ley = lex;
+            x = xn;
+            lx = lxn;
+            tx = txn;
+            if (++steps > w.max_rot) {
+                atomicOr(&w.ctrl->error, DEV_ERR_NONTERMINATING);
+                break;
+            }
+        }
+        const uint32_t dx = (uint32_t)(x - eb);
+        if (dx < (uint32_t)nE) s_pv[dx] = e;
+        else if (!BATCH) m.prev[x] = e;
+        else w.loc_prev[__ldg(w.loc_h_off + mj) + (x - sh)] = e - sh;  // e, x lie in mesh mj
+        if (x == twk) {
+            const int32_t sl = atomicAdd(&w.ctrl->n_tips, 1);
+            if (sl < w.tip_cap) w.tips[sl] = twk;
+            else atomicOr(&w.ctrl->error, DEV_ERR_CAPACITY);
+        }
+    }
+    __syncthreads();  // every prev slot is final
+    // walk-start marks: frontier, next and prev larger (prev -1: set by
+    // another CTA, counted as larger)
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int32_t e = e0 + k;
+            const int32_t nk = (uint32_t)k == kt ? x : e0 + (k == 2 ? 0 : k + 1);
+            const int32_t pk = s_pv[lb + k];
+            if (((F >> k) & 1u) && nk > e && (pk < 0 || pk > e)) fl |= 8u << k;
+            s_nx[lb + k] = nk;
+        }
+        w.flags[t] = (uint8_t)fl;
+    }
+    __syncwarp();
+    // each warp stores the links of its 96 half-edges in place, coalesced
+    // (in a batch, also in the meshes' own indices and arrays; a batch's
+    // union prev is never read, so it is not written)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t bj = BATCH ? s_m0 : 0;
+    for (int i = lane; i < 96; i += 32) {
+        const int32_t sl = 96 * wid + i;
+        if (sl >= nE) break;
+        const int32_t xe = eb + sl;
+        const int32_t nv = s_nx[sl];
+        const int32_t pv = s_pv[sl];
+        m.next[xe] = nv;
+        if (!BATCH) {
+            if (pv >= 0) m.prev[xe] = pv;
+        } else {
+            while (bj + 1 < w.loc_n && 3 * __ldg(w.loc_t_off + bj + 1) <= xe) bj++;
+            const int32_t shj = 3 * __ldg(w.loc_t_off + bj);
+            const int32_t g = __ldg(w.loc_h_off + bj) + (xe - shj);
+            w.loc_next[g] = nv - shj;
+            if (pv >= 0) w.loc_prev[g] = pv - shj;
+        }
+    }
+}
+
+// launch configurations: (triangles per CTA, triangles per thread); one per
+// thread runs k_label_relink1, more run k_label_relink
+#define RELINK1_CONFIGS(X) \
+    X(64)                  \
+    X(128)                 \
+    X(256)
 #define RELINK_CONFIGS(X) \
-    X(64, 1)              \
-    X(128, 1)             \
-    X(256, 1)             \
     X(128, 2)             \
     X(64, 4)
 
 bool relink_config_valid(int32_t tile, int32_t items) {
+#define X(N) \
+    if (tile == N && items == 1) return true;
+    RELINK1_CONFIGS(X)
+#undef X
 #define X(N, I) \
     if (tile == N * I && items == I) return true;
     RELINK_CONFIGS(X)
@@ -628,6 +791,14 @@ bool relink_config_valid(int32_t tile, int32_t items) {
 int relink_configure() { return 0; }  // static shared memory only
 
 void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
+#define X(N)                                                                         \
+    if (w.rl_tile == N && w.rl_items == 1) {                                         \
+        if (w.loc_n > 0) k_label_relink1<N, true><<<(m.T + N - 1) / N, N, 0, s>>>(m, w); \
+        else k_label_relink1<N, false><<<(m.T + N - 1) / N, N, 0, s>>>(m, w);       \
+        return;                                                                      \
+    }
+    RELINK1_CONFIGS(X)
+#undef X
 #define X(N, I)                                                                      \
     if (w.rl_tile == N * I && w.rl_items == I) {                                     \
         if (w.loc_n > 0) k_label_relink<N, I, true><<<(m.T + N * I - 1) / (N * I), N, 0, s>>>(m, w);  \
@@ -636,8 +807,8 @@ void launch_label_relink(const MeshView &m, const Work &w, cudaStream_t s) {
     }
     RELINK_CONFIGS(X)
 #undef X
-    if (w.loc_n > 0) k_label_relink<128, 1, true><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
-    else k_label_relink<128, 1, false><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
+    if (w.loc_n > 0) k_label_relink1<128, true><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
+    else k_label_relink1<128, false><<<(m.T + 127) / 128, 128, 0, s>>>(m, w);
 }
 
 }  // namespace polylla

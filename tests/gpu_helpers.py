@@ -8,14 +8,17 @@ import numpy as np
 from paper_2403_14723_gb300 import build, polylla
 
 
-def gpu_run(mesh, generate_times: int = 1, max_rotation: int = 0) -> dict:
-    """Upload ``mesh``, run polylla_generate ``generate_times`` times and
+def gpu_run(mesh, generate_times: int = 1, max_rotation: int = 0, tuning: dict | None = None) -> dict:
+    """Upload ``mesh``, run polylla_generate ``generate_times`` times (with
+    the launch settings ``tuning`` overriding the current ones, if given) and
     return every output as numpy arrays."""
     import torch
 
     build.build_library()
     dm = polylla.DeviceMesh.from_host(mesh)
     with polylla.Polylla(dm, max_rotation=max_rotation) as p:
+        if tuning:
+            polylla.polylla_set_tuning(p.ctx, dict(polylla.polylla_get_tuning(p.ctx), **tuning))
         for _ in range(generate_times):
             p.generate()
         out = p.polygons()

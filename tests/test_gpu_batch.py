@@ -39,7 +39,7 @@ def _mix():
     return ms
 
 
-def batch_run(meshes, graph=False, tune=False, generate_times=1, unaligned=False):
+def batch_run(meshes, graph=False, tune=False, generate_times=1, unaligned=False, tuning=None):
     import torch
 
     build.build_library()
@@ -59,6 +59,8 @@ def batch_run(meshes, graph=False, tune=False, generate_times=1, unaligned=False
         try:
             if tune:
                 polylla.polylla_autotune(ctx, reps=2, stream=stream)
+            if tuning:
+                polylla.polylla_set_tuning(ctx, dict(polylla.polylla_get_tuning(ctx), **tuning))
             if graph:
                 polylla.polylla_capture_graph(ctx, stream)
             for _ in range(generate_times):
@@ -116,6 +118,19 @@ def test_batch_with_unaligned_local_arrays():
 def test_batch_generate_twice_and_from_a_graph():
     meshes = _mix()
     db, g = batch_run(meshes, graph=True, generate_times=2)
+    assert_batch_parity(meshes, db, g)
+
+
+# every relink launch setting: one triangle per thread (64, 128 or 256 per
+# CTA) runs the one-rotation-per-thread kernel, two or four per thread the
+# kernel with per-warp rotation lists
+RELINK_SETTINGS = [(64, 1), (128, 1), (256, 1), (256, 2), (256, 4)]
+
+
+@pytest.mark.parametrize("tile,items", RELINK_SETTINGS)
+def test_batch_every_relink_setting(tile, items):
+    meshes = _mix()
+    db, g = batch_run(meshes, tuning={"relink_tile": tile, "relink_items": items})
     assert_batch_parity(meshes, db, g)
 
 

@@ -102,6 +102,17 @@ def test_parity_random_sweep():
         assert_parity(mesh, g, oracle.run_mesh(mesh))
 
 
+@pytest.mark.parametrize("tile,items", [(64, 1), (128, 1), (256, 1), (256, 2), (256, 4)])
+def test_parity_every_relink_setting(tile, items):
+    """Every relink launch setting (triangles per CTA, per thread) gives the
+    oracle's arrays on meshes with barrier tips, exact ties and a ragged
+    last CTA."""
+    for mesh in [meshgen.random_delaunay(3000, seed=77), meshgen.perturbed_grid(61, 0.3, seed=5),
+                 _lattice(500), _near_tie(2)] + _tip_meshes(2):
+        g = gpu_run(mesh, tuning={"relink_tile": tile, "relink_items": items})
+        assert_parity(mesh, g, oracle.run_mesh(mesh))
+
+
 def test_parity_generate_is_repeatable():
     """generate never reads the input next/prev of interior half-edges, so a
     second and third call on the rewritten arrays give the same result."""
