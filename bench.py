@@ -203,16 +203,17 @@ def core_kernel_digest() -> str:
     return build.core_digest()
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu summary,
-    if it was taken on the current kernel sources (else None)."""
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of ``kernel`` on ``workload`` from the committed
+    ncu summary, if the summary is scaled to that workload and was taken on
+    the current kernel sources (else None)."""
     from paper_2403_14723_gb300 import build
 
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("core_kernel_digest") != build.core_digest():
+    if d.get("core_kernel_digest") != build.core_digest() or d.get("workload") != workload:
         return None
     k = d.get("kernels", {}).get(kernel)
     if not k:
@@ -408,13 +409,13 @@ def run_gb300(args):
     dominant = max(stage_ms, key=stage_ms.get)
     peak, peak_kind = measured_peaks()
     ach = per_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
-    traffic = ncu_traffic(dominant)
+    traffic = ncu_traffic(dominant, args.workload)
     kernels = {}
     for k, t_ms in stage_ms.items():
         if t_ms <= 0.0:
             continue
         share = per_stage.get(k, 0)
-        tr = ncu_traffic(k)
+        tr = ncu_traffic(k, args.workload)
         kernels[k] = {"ms": t_ms, "share_bytes": share,
                       "frac": (share / (t_ms * 1e-3) / 1e9 / peak) if share else None,
                       "traffic": tr, "traffic_over_share": (tr / share) if (tr and share) else None}
@@ -794,7 +795,7 @@ def run_batched(args):
     peak, peak_kind = measured_peaks()
     ach = per_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": ncu_traffic(dominant),
+                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs", "traffic": ncu_traffic(dominant, args.workload),
                 "algorithmic_bytes": per_stage[dominant], "stage_ms": stage_ms,
                 "whole_step": {"algorithmic_bytes": total_alg, "achieved": total_alg / (ms * 1e-3) / 1e9,
                                "frac": total_alg / (ms * 1e-3) / 1e9 / peak}}

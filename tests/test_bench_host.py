@@ -73,3 +73,23 @@ def test_batch_trace_summarises_the_log():
     assert len(log) - tr["lane_batches"] == 2
     assert tr["meta_notice_delay_ms"]["max"] == pytest.approx(0.01, abs=1e-3)
     assert tr["stream_start_delay_ms"]["max"] == pytest.approx(0.01, abs=1e-3)
+
+
+def test_roofline_traffic_only_for_the_profiled_workload_and_kernels():
+    """The bench line's per-kernel DRAM traffic comes from the committed ncu
+    summary only for the workload that summary is scaled to, and only while
+    the method kernels hash to the digest it records; the shares it is
+    compared with sum to B_alg."""
+    from paper_2403_14723_gb300 import build
+
+    d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    wl = d["workload"]
+    for k, rec in d["kernels"].items():
+        want = rec["dram_bytes_per_launch_full_workload"] if d["core_kernel_digest"] == build.core_digest() else None
+        assert bench.ncu_traffic(k, wl) == want
+        assert bench.ncu_traffic(k, "pgrid_2048") is None
+        assert bench.ncu_traffic(k, "batch_4096") is None
+    assert bench.ncu_traffic("no_such_kernel", wl) is None
+    T, V, NF, P = 33_538_050, 16_777_216, 59_815_876, 13_138_913
+    total, per = bench.algorithmic_bytes(T, V, NF, P)
+    assert total == 24 * T + 16 * V + 16 * NF + 8 * P and sum(per.values()) == total
