@@ -62,7 +62,7 @@ void launch_validate(const MeshView &m, int32_t *bad, cudaStream_t s) {
 // Filter.  Each coordinate x is truncated to float32 (x^ keeps the top 23
 // significand bits, so |x^ - x| <= 2^-23 |x| = 2u|x| with u = 2^-24, and
 // |x^| <= |x|) by bit manipulation (no float64 instruction); coordinates
-// outside [2^-126, 2^60) in magnitude (zero included) send the triangle to
+// outside [2^-126, 2^61) in magnitude (zero included) send the triangle to
 // the float64 path.  With S = |x^a| + |x^b| the float32 difference
 // dx^ = fl32(x^b - x^a) satisfies |dx^ - dx| <= 3.0001 u Sx, hence
 //   |D^ - d| <= 6.0003u (Sx|dx^| + Sy|dy^|) + 9.0007u^2 (Sx^2 + Sy^2)

@@ -211,13 +211,13 @@ __device__ __forceinline__ int32_t mesh_of(const int32_t *seg, const int32_t *t_
 // ---- float32 filters of float64 decisions -----------------------------------
 // v truncated to float32: the top 23 significand bits, so |v^ - v| <= 2^-23
 // |v^| and |v^| <= |v|, by bit manipulation (no float64 instruction).  A
-// magnitude outside [2^-126, 2^60) (zero included) sets bad: the caller then
+// magnitude outside [2^-126, 2^61) (zero included) sets bad: the caller then
 // takes its exact float64 path.
 __device__ __forceinline__ float trunc_to_f32(double v, uint32_t &bad) {
     uint32_t hi = (uint32_t)__double2hiint(v);
     uint32_t lo = (uint32_t)__double2loint(v);
     uint32_t mag = hi & 0x7FFFFFFFu;
-    // biased float64 exponent must lie in [897, 1083]: |v| in [2^-126, 2^60)
+    // biased float64 exponent must lie in [897, 1083]: |v| in [2^-126, 2^61)
     bad |= (uint32_t)((mag - (897u << 20)) >= ((1084u - 897u) << 20));
     // (hi:lo) << 3 puts the low 9 exponent bits at 31..23 and the top 23
     // significand bits at 22..0; subtracting 384 from that 9-bit field
