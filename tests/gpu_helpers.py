@@ -8,21 +8,30 @@ import numpy as np
 from paper_2403_14723_gb300 import build, polylla
 
 
-def gpu_run(mesh, generate_times: int = 1, max_rotation: int = 0, tuning: dict | None = None) -> dict:
+def gpu_run(mesh, generate_times: int = 1, max_rotation: int = 0, tuning: dict | None = None,
+            as_benched: bool = False) -> dict:
     """Upload ``mesh``, run polylla_generate ``generate_times`` times (with
-    the launch settings ``tuning`` overriding the current ones, if given) and
-    return every output as numpy arrays."""
+    the launch settings ``tuning`` overriding the current ones, if given; or,
+    with ``as_benched``, as bench.py times it: on a side stream, autotuned,
+    from a captured CUDA graph) and return every output as numpy arrays."""
     import torch
 
     build.build_library()
     dm = polylla.DeviceMesh.from_host(mesh)
-    with polylla.Polylla(dm, max_rotation=max_rotation) as p:
+    stream = torch.cuda.Stream() if as_benched else torch.cuda.current_stream()
+    with torch.cuda.stream(stream), polylla.Polylla(dm, max_rotation=max_rotation, stream=stream) as p:
         if tuning:
             polylla.polylla_set_tuning(p.ctx, dict(polylla.polylla_get_tuning(p.ctx), **tuning))
+        if as_benched:
+            polylla.polylla_autotune(p.ctx, reps=2, stream=stream)
+            polylla.polylla_capture_graph(p.ctx, stream)
+            dm.next[:3 * mesh.n_triangles].fill_(-1)   # generate never reads interior next/prev
+            dm.prev[:3 * mesh.n_triangles].fill_(-1)
         for _ in range(generate_times):
-            p.generate()
-        out = p.polygons()
-        lab = p.labels()
+            p.generate(stream)
+        out = p.polygons(stream)
+        lab = p.labels(stream)
+        stream.synchronize()
         torch.cuda.synchronize()
         res = {
             "n_polygons": out["n_polygons"], "n_frontier": out["n_frontier"],

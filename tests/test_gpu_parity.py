@@ -132,7 +132,9 @@ def test_parity_delaunay_1m():
 
 def test_parity_perturbed_grid_4096():
     """The 4096 x 4096 perturbed grid (33.5M triangles): every array, full
-    size, plus the output invariants."""
+    size, plus the output invariants; then again in the launch
+    configuration bench.py times (autotuned, from a CUDA graph, on a side
+    stream)."""
     mesh = meshgen.workload("pgrid_4096")
     g = gpu_run(mesh)
     r = oracle.run_mesh(mesh)
@@ -140,6 +142,12 @@ def test_parity_perturbed_grid_4096():
     checks.check_output_invariants(
         mesh, r.frontier1, g["next"], g["prev"], g["seeds"], g["offsets"], g["he_list"], g["v_list"],
         n_seeds_alg4=len(r.seed_list), n_distinct_chords=r.stats["distinct_chords"])
+    del g
+    try:
+        g = gpu_run(mesh, as_benched=True)
+    finally:
+        polylla.polylla_tuning_cache_clear()
+    assert_parity(mesh, g, r)
 
 
 def test_rejects_corrupt_mesh():
